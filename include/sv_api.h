@@ -1,0 +1,256 @@
+/*
+ * sv_api.h -- C ABI of the GB300 state-vector simulator (libsv.so).
+ *
+ * The library keeps the full vector of 2^n complex amplitudes resident in GPU
+ * memory and applies gates to it in place.  The paper this follows describes
+ * a Schroedinger simulator as exactly that: the state of an n-qubit circuit is
+ * a 2^n complex vector, every circuit moment is a 2^n x 2^n matrix, and
+ * simulation is matrix-vector multiplication whose cost grows linearly with
+ * the number of gates (Sec. I-A "Background"; Sec. II "Methods", assumption
+ * (a)).  Keeping the state on the device avoids the CPU<->GPU transfer cost
+ * the paper identifies as the reason GPU simulation loses at small widths
+ * (Sec. III, opening discussion); only scalars, samples and the small
+ * circuit description cross the host link.
+ *
+ * Conventions shared by every entry point:
+ *   - qubit q is bit q of the amplitude index (little-endian);
+ *   - amplitudes are interleaved (re, im): SV_C64 = 2 x float (8 B per
+ *     amplitude), SV_C128 = 2 x double (16 B per amplitude);
+ *   - a k-qubit gate matrix is row-major 2^k x 2^k complex FP64 on the host,
+ *     interleaved (re, im); bit j of its row/column index is targets[j];
+ *   - a gate acts only where every control qubit is |1>.
+ *
+ * Ownership: the caller owns every device buffer (amplitudes, workspace) and
+ * every host buffer.  A state handle borrows its buffers and must be
+ * destroyed before they are freed.  The handle itself owns only host metadata
+ * (plan caches, a pinned staging buffer, CUDA events).
+ *
+ * Streams: all work is enqueued on the stream given to sv_create.  Calls
+ * returning host values (expectations, norms, samples, gradients)
+ * synchronise that stream before they return; the others return as soon as
+ * the work is enqueued.
+ *
+ * Errors: every entry point returns an sv_status; nothing throws or aborts
+ * across the ABI.  Arguments are validated on the host before anything is
+ * enqueued (qubits in range and distinct, controls disjoint from targets,
+ * sizes, alignment).  On failure, sv_last_error() returns a thread-local
+ * message describing the last error of the calling thread.  Device-side
+ * waits are bounded: a wait that runs out sets a device flag and the call
+ * reports SV_ETIMEOUT.
+ */
+#ifndef SV_API_H
+#define SV_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SV_OK = 0,
+  SV_EINVAL = 1,        /* bad argument (qubits, sizes, pointers, alignment) */
+  SV_ENOMEM = 2,        /* workspace too small, or a host allocation failed */
+  SV_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  SV_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
+  SV_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+/* Arithmetic used for dense fused blocks of 4..6 qubits (complex64 states
+ * only; complex128 states always use FP64 CUDA-core arithmetic). */
+typedef enum {
+  SV_PREC_PLAIN = 0,       /* FP32 FMA on CUDA cores */
+  SV_PREC_TC_BF16X3 = 1,   /* tensor cores, split-BF16 (3 products), FP32 accumulate */
+  SV_PREC_TC_TF32X3 = 2    /* tensor cores, split-TF32 (3 products), FP32 accumulate */
+} sv_prec;
+
+/* Named gates (matrices built by the library in FP64; readings as in the
+ * library documentation: U3 is OpenQASM's, SX/SY/SW are ((1+i)/2)(I - iP),
+ * FSIM(theta, phi) acts on |01>,|10> with cos(theta), -i sin(theta) and
+ * puts e^{-i phi} on |11>). */
+typedef enum {
+  SV_GATE_MATRIX = 0,   /* explicit matrix from sv_circuit.matrices */
+  SV_GATE_H = 1, SV_GATE_X, SV_GATE_Y, SV_GATE_Z, SV_GATE_S, SV_GATE_SDG, SV_GATE_T,
+  SV_GATE_TDG, SV_GATE_SX, SV_GATE_SY, SV_GATE_SW, SV_GATE_ID,
+  SV_GATE_RX = 20, SV_GATE_RY, SV_GATE_RZ, SV_GATE_PHASE,  /* one angle */
+  SV_GATE_U3 = 30,                                         /* three angles */
+  SV_GATE_CZ = 40, SV_GATE_SWAP,                           /* two targets */
+  SV_GATE_FSIM = 50                                        /* two targets, two angles */
+} sv_gate;
+
+typedef struct {
+  int32_t gate;          /* sv_gate */
+  int32_t n_targets;     /* 1..6 */
+  int32_t n_controls;    /* 0..8 */
+  int32_t param;         /* -1, or index into the parameter vector: angles[0] := params[param] */
+  int32_t targets[6];
+  int32_t controls[8];
+  double angles[3];
+  int64_t matrix_offset; /* SV_GATE_MATRIX: offset, in complex entries, into sv_circuit.matrices */
+} sv_op;
+
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_ops;
+  int32_t n_params;
+  int32_t reserved;
+  const sv_op *ops;          /* host array of n_ops */
+  const double *matrices;    /* host FP64 interleaved complex pool (may be NULL if unused) */
+} sv_circuit;
+
+typedef enum {
+  SV_MODE_TILED = 0,     /* fuse gates into blocks, group blocks into shared-memory tile passes */
+  SV_MODE_PER_GATE = 1   /* one global-memory pass per (fused) block */
+} sv_mode;
+
+typedef struct {
+  int32_t fusion_k;          /* 0 = default, 1 = no fusion, 2..6 = max qubits per fused block */
+  int32_t tile_m;            /* 0 = default; else qubits held per shared-memory tile */
+  int32_t prec;              /* sv_prec */
+  int32_t mode;              /* sv_mode */
+  uint64_t timeout_cycles;   /* 0 = default budget for bounded device waits */
+} sv_options;
+
+/* Pauli string: X on the bits of x_mask, Z on the bits of z_mask, Y where both
+ * are set (P = i^{popcount(x&z)} X^x Z^z). */
+typedef struct {
+  uint64_t x_mask;
+  uint64_t z_mask;
+  double coeff;
+} sv_pauli_term;
+
+typedef struct sv_state sv_state;
+
+/* ---------------------------------------------------------------------------
+ * State handles (Sec. I-A: the state is the vector of 2^n amplitudes)
+ * ------------------------------------------------------------------------- */
+
+/* Workspace bytes a state of this size needs for reductions, sampling and
+ * uploaded gate programs. */
+size_t sv_workspace_bytes(int n_qubits, sv_dtype dtype);
+
+/* Wrap caller-owned device memory as a state.
+ *   amps_dev:  >= 2^n amplitudes of `dtype`, 256-byte aligned.
+ *   ws_dev:    >= sv_workspace_bytes(n, dtype), 256-byte aligned.
+ *   stream:    a cudaStream_t (NULL = legacy default stream).
+ * The amplitudes are not initialised.  n_qubits in [1, 34].
+ * Errors: SV_EINVAL (sizes, alignment, n), SV_ENOMEM (workspace), SV_ECUDA. */
+sv_status sv_create(int n_qubits, sv_dtype dtype, void *amps_dev, size_t amps_bytes,
+                    void *ws_dev, size_t ws_bytes, void *stream, sv_state **out);
+sv_status sv_destroy(sv_state *s);
+
+/* psi := |index>  (one write pass).  SV_EINVAL if index >= 2^n. */
+sv_status sv_set_basis(sv_state *s, uint64_t index);
+/* Copy 2^n amplitudes host -> device / device -> host (bytes must equal the
+ * state size); synchronous w.r.t. the host.  Used for checkpoints and for
+ * end-to-end runs that start from a host state. */
+sv_status sv_upload(sv_state *s, const void *host, size_t bytes);
+sv_status sv_download(sv_state *s, void *host, size_t bytes);
+/* Wait for all work enqueued on the state's stream; reports device-side
+ * timeouts raised by earlier calls. */
+sv_status sv_synchronize(sv_state *s);
+
+/* ---------------------------------------------------------------------------
+ * Gate application (Sec. II: simulation is matrix-vector multiplication)
+ * ------------------------------------------------------------------------- */
+
+/* Apply one k-qubit gate (k = 1..6) with nctrl controls (0..8) in place.
+ * matrix: host FP64 2^k x 2^k complex, row-major, interleaved.  If adjoint
+ * is nonzero the conjugate transpose is applied.  The matrix is assumed
+ * unitary (not checked).  Errors: SV_EINVAL for qubits out of range,
+ * duplicated, or controls overlapping targets. */
+sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_t *controls,
+                        int nctrl, const double *matrix, int adjoint);
+
+/* Apply a whole circuit in place: gates are fused into dense blocks of at
+ * most opt->fusion_k qubits (products formed in FP64 on the host; gates only
+ * move across gates on disjoint qubits), then grouped into shared-memory tile
+ * passes so that each pass reads and writes the state once.
+ *   params: host FP64 vector of c->n_params (may be NULL if none is used).
+ *   opt:    may be NULL (defaults).
+ * Errors: SV_EINVAL (malformed op, width mismatch), SV_ENOMEM (program does
+ * not fit the workspace). */
+sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params,
+                           const sv_options *opt);
+
+/* Apply the same circuit structure to B states (each with its own parameter
+ * vector params[b], host FP64, may be NULL) in one launch sequence.  States
+ * may have different widths only if circuits differ (circs[b] matches
+ * states[b]); all states must share the first state's stream and device.
+ * Work for all states is scheduled by one persistent kernel per pass
+ * wave.  Errors as sv_apply_circuit. */
+sv_status sv_apply_circuit_batch(sv_state *const *states, int B, const sv_circuit *const *circs,
+                                 const double *const *params, const sv_options *opt);
+
+/* ---------------------------------------------------------------------------
+ * Observables (Sec. I: simulated output values feed an error function)
+ * ------------------------------------------------------------------------- */
+
+/* out = sum_t coeff_t Re <psi|P_t|psi>; products in the state's precision,
+ * accumulated in FP64.  Synchronises.  SV_EINVAL for masks beyond n. */
+sv_status sv_expect(sv_state *s, const sv_pauli_term *terms, int n_terms, double *out_host);
+/* out[q] = <Z_q> for q = 0..n-1 in one read pass.  Synchronises. */
+sv_status sv_expect_z_all(sv_state *s, double *out_host);
+/* norm2 = sum_x |psi_x|^2 (FP64 accumulation).  Synchronises. */
+sv_status sv_norm(sv_state *s, double *norm2_out);
+/* psi := psi / sqrt(sum |psi|^2); optionally returns the old norm^2. */
+sv_status sv_renormalize(sv_state *s, double *norm2_out);
+/* Measurement sampling: shot j returns the smallest x with
+ * CDF(x) > u_j * sum|psi|^2, CDF the inclusive prefix sum of |psi_x|^2 in
+ * index order (FP64), u_j = (SplitMix64(seed, j) >> 11) * 2^-53 where
+ * SplitMix64(seed, j) is the j-th output of the sequential SplitMix64
+ * generator seeded with `seed`.  out_host: n_shots uint64.  Synchronises. */
+sv_status sv_sample(sv_state *s, int64_t n_shots, uint64_t seed, uint64_t *out_host);
+
+/* ---------------------------------------------------------------------------
+ * Differentiation (Sec. I: variational training needs the error function's
+ * parameter gradient)
+ * ------------------------------------------------------------------------- */
+
+/* Adjoint-method gradient of E(theta) = <psi_out|H|psi_out>,
+ * psi_out = circuit(theta) psi_in:  forward sweep on psi, lambda = H psi,
+ * then a reverse sweep that un-applies each gate from both vectors and adds
+ * Im<lambda|G_j|psi> for each parametric gate U_j = exp(-i theta G_j / 2)
+ * (RX, RY, RZ; PHASE with G = diag(0, -2)); no tape of states is kept.
+ *   psi:            in = psi_in; out = psi_out.
+ *   lambda_scratch: a state of the same width and dtype (clobbered).
+ *   params:         host FP64, c->n_params.
+ *   expval_out:     host double; grad_out: host double[c->n_params].
+ * Parametric gates must be uncontrolled single-qubit RX/RY/RZ/PHASE
+ * (SV_EUNSUPPORTED otherwise).  Synchronises. */
+sv_status sv_adjoint_grad(sv_state *psi, sv_state *lambda_scratch, const sv_circuit *c,
+                          const double *params, const sv_pauli_term *terms, int n_terms,
+                          const sv_options *opt, double *expval_out, double *grad_out);
+
+/* Batched form: B parameter sets of one circuit, psi[b] / lam[b] as above,
+ * params row-major B x n_params, expval_out[B], grad_out row-major
+ * B x n_params.  All states must have the same width, dtype and stream. */
+sv_status sv_adjoint_grad_batch(sv_state *const *psi, sv_state *const *lam, int B,
+                                const sv_circuit *c, const double *params,
+                                const sv_pauli_term *terms, int n_terms, const sv_options *opt,
+                                double *expval_out, double *grad_out);
+
+/* ---------------------------------------------------------------------------
+ * Runtime services
+ * ------------------------------------------------------------------------- */
+
+/* Time candidate (fusion_k, tile_m) pairs for this circuit on `scratch`
+ * (its contents are clobbered) and write the fastest into *inout.  Results
+ * are cached per (n, dtype, circuit shape) in memory and, if the
+ * SV_TUNE_CACHE environment variable names a file, in that JSON file. */
+sv_status sv_autotune(sv_state *scratch, const sv_circuit *c, sv_options *inout);
+
+/* Number of kernels this library has launched in this process (all
+ * devices).  Lets callers count device work without a profiler. */
+uint64_t sv_kernel_launch_count(void);
+
+const char *sv_last_error(void);
+const char *sv_status_string(sv_status st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_API_H */

@@ -1,0 +1,463 @@
+// K8-K10 and state set-up: basis initialisation, scaling, norm, Pauli-string
+// expectations, all-qubit <Z_q>, and inverse-CDF sampling.
+//
+// Reductions form products in the state's precision and accumulate short
+// runs (16 amplitudes) in that precision before adding into FP64; block and
+// grid levels are FP64 throughout.  Sampling computes |psi_x|^2 in FP64 so
+// the cumulative distribution is the one an FP64 reference would build from
+// the same amplitudes.
+#include <algorithm>
+
+#include "sv_device.cuh"
+#include "sv_internal.h"
+
+namespace sv {
+
+constexpr int kRedThreads = 256;
+
+static int red_grid(sv_state *s, uint64_t work) {
+  const uint64_t want = (work + kRedThreads - 1) / kRedThreads;
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)s->sm_count * 4));
+}
+int red_blocks_max(sv_state *s) { return s->sm_count * 4; }
+
+// ---- basis state / scaling -----------------------------------------------
+template <typename R>
+__global__ void k_set_basis(int4 *__restrict__ a, uint64_t nunits, uint64_t index) {
+  using C = typename Cx<R>::T;
+  constexpr uint64_t APU = 16 / sizeof(C);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t hit = index / APU;
+  for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nunits; u += stride) {
+    int4 z = make_int4(0, 0, 0, 0);
+    if (u == hit) {
+      C v[APU];
+      for (uint64_t j = 0; j < APU; j++) v[j] = czero<C>();
+      v[index % APU].x = R(1);
+      z = *reinterpret_cast<int4 *>(v);
+    }
+    __stcs(a + u, z);
+  }
+}
+
+template <typename R>
+__global__ void k_scale(typename Cx<R>::T *__restrict__ a, uint64_t namps, R f) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < namps; i += stride) {
+    auto v = a[i];
+    v.x *= f;
+    v.y *= f;
+    a[i] = v;
+  }
+}
+
+sv_status launch_set_basis(sv_state *s, uint64_t index) {
+  const uint64_t nunits = ((1ull << s->n) * amp_bytes(s->dt) + 15) / 16;
+  const int g = std::min<uint64_t>((nunits + kRedThreads - 1) / kRedThreads, (uint64_t)s->sm_count * 8);
+  if (s->dt == SV_C64)
+    k_set_basis<float><<<std::max(g, 1), kRedThreads, 0, s->stream>>>((int4 *)s->amps, nunits, index);
+  else
+    k_set_basis<double><<<std::max(g, 1), kRedThreads, 0, s->stream>>>((int4 *)s->amps, nunits, index);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+sv_status launch_scale(sv_state *s, double f) {
+  const uint64_t na = 1ull << s->n;
+  const int g = red_grid(s, na);
+  if (s->dt == SV_C64)
+    k_scale<float><<<g, kRedThreads, 0, s->stream>>>((float2 *)s->amps, na, (float)f);
+  else
+    k_scale<double><<<g, kRedThreads, 0, s->stream>>>((double2 *)s->amps, na, f);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+// ---- block reduction helpers ---------------------------------------------
+__device__ __forceinline__ void block_sum_to(double v, double *dst) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+    t = warp_sum(t);
+    if (l == 0) *dst = t;
+  }
+}
+
+// out[j] = sum_b partial[b * nvals + j]  (+ optional add into out)
+__global__ void k_finalize(const double *__restrict__ partial, int nblocks, int nvals, double *out) {
+  for (int j = threadIdx.x; j < nvals; j += blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < nblocks; b++) s += partial[(size_t)b * nvals + j];
+    out[j] = s;
+  }
+}
+
+// ---- norm -----------------------------------------------------------------
+template <typename R>
+__global__ void k_norm(const int4 *__restrict__ a, uint64_t nunits, double *partial) {
+  using C = typename Cx<R>::T;
+  constexpr int APU = 16 / sizeof(C);
+  constexpr int RUN = 8;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc = 0;
+  for (uint64_t u0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u0 < nunits; u0 += RUN * stride) {
+    R run = 0;
+#pragma unroll
+    for (int j = 0; j < RUN; j++) {
+      const uint64_t u = u0 + j * stride;
+      if (u < nunits) {
+        int4 raw = __ldcs(a + u);
+        const C *v = reinterpret_cast<const C *>(&raw);
+#pragma unroll
+        for (int e = 0; e < APU; e++) run += v[e].x * v[e].x + v[e].y * v[e].y;
+      }
+    }
+    acc += (double)run;
+  }
+  block_sum_to(acc, partial + blockIdx.x);
+}
+
+sv_status launch_norm(sv_state *s, double *out_dev) {
+  const uint64_t nunits = ((1ull << s->n) * amp_bytes(s->dt) + 15) / 16;
+  double *partial = reinterpret_cast<double *>(s->ws + kWsRed);
+  const int g = red_grid(s, nunits / 8 + 1);
+  if (s->dt == SV_C64)
+    k_norm<float><<<g, kRedThreads, 0, s->stream>>>((const int4 *)s->amps, nunits, partial);
+  else
+    k_norm<double><<<g, kRedThreads, 0, s->stream>>>((const int4 *)s->amps, nunits, partial);
+  k_finalize<<<1, 32, 0, s->stream>>>(partial, g, 1, out_dev);
+  g_launches += 2;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+// ---- Pauli-string group expectation --------------------------------------
+// For one x_mask: sum_x Re( conj(psi[x ^ xm]) * F(x) * psi[x] ),
+// F(x) = sum_t c_t i^{k_t} (-1)^{popcount(x & zm_t)}.
+constexpr int kMaxGroupTerms = 64;
+struct ExpectArgs {
+  uint64_t xm;
+  int nt;
+  uint64_t zm[kMaxGroupTerms];
+  double fr[kMaxGroupTerms], fi[kMaxGroupTerms];
+};
+
+template <typename R>
+__global__ void k_expect(const typename Cx<R>::T *__restrict__ a, uint64_t namps,
+                         const __grid_constant__ ExpectArgs A, double *partial) {
+  using C = typename Cx<R>::T;
+  constexpr int RUN = 16;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc = 0;
+  for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x0 < namps; x0 += RUN * stride) {
+    R run = 0;
+#pragma unroll 4
+    for (int j = 0; j < RUN; j++) {
+      const uint64_t x = x0 + j * stride;
+      if (x >= namps) break;
+      const C v = a[x], w = a[x ^ A.xm];
+      R fr = 0, fi = 0;
+      for (int t = 0; t < A.nt; t++) {
+        const R sg = (__popcll(x & A.zm[t]) & 1) ? R(-1) : R(1);
+        fr += sg * (R)A.fr[t];
+        fi += sg * (R)A.fi[t];
+      }
+      // Re(conj(w) * (f * v))
+      const R pr = fr * v.x - fi * v.y, pi = fr * v.y + fi * v.x;
+      run += w.x * pr + w.y * pi;
+    }
+    acc += (double)run;
+  }
+  block_sum_to(acc, partial + blockIdx.x);
+}
+
+sv_status launch_expect_group(sv_state *s, uint64_t xm, const uint64_t *zm, const double *cf,
+                              const int *ipow, int nt, double *out_dev) {
+  if (nt > kMaxGroupTerms) return set_error(SV_EINVAL, "too many terms in one group");
+  ExpectArgs A{};
+  A.xm = xm;
+  A.nt = nt;
+  for (int t = 0; t < nt; t++) {
+    A.zm[t] = zm[t];
+    switch (ipow[t] & 3) {
+      case 0: A.fr[t] = cf[t]; break;
+      case 1: A.fi[t] = cf[t]; break;
+      case 2: A.fr[t] = -cf[t]; break;
+      default: A.fi[t] = -cf[t]; break;
+    }
+  }
+  const uint64_t na = 1ull << s->n;
+  double *partial = reinterpret_cast<double *>(s->ws + kWsRed);
+  const int g = red_grid(s, na / 16 + 1);
+  if (s->dt == SV_C64)
+    k_expect<float><<<g, kRedThreads, 0, s->stream>>>((const float2 *)s->amps, na, A, partial);
+  else
+    k_expect<double><<<g, kRedThreads, 0, s->stream>>>((const double2 *)s->amps, na, A, partial);
+  k_finalize<<<1, 32, 0, s->stream>>>(partial, g, 1, out_dev);
+  g_launches += 2;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+// ---- <Z_q> for every qubit in one pass -----------------------------------
+// A warp sweeps chunks of 8 x 32 16-byte units.  Index bits inside a unit,
+// the 5 lane bits and the 3 trip bits are resolved with FP32 warp sums; the
+// bits above are constant over a chunk.  Lane q keeps the FP64 running sum
+// S_q = sum over amplitudes with bit q set (lanes 0..31 and, for n > 32,
+// a second register for q + 32).  <Z_q> = total - 2 S_q.
+template <typename R>
+__global__ void k_zall(const int4 *__restrict__ a, int n, uint64_t nchunks, double *partial) {
+  using C = typename Cx<R>::T;
+  constexpr int APU = 16 / sizeof(C);
+  constexpr int LB = APU == 2 ? 1 : 0;  // index bits inside a unit
+  constexpr int TRIPS = 8;
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  double S0 = 0, S1 = 0, T = 0;
+  for (uint64_t ch = warp; ch < nchunks; ch += nwarps) {
+    const uint64_t ubase = ch * (32 * TRIPS);
+    R tot = 0, b0 = 0, bj[3] = {0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < TRIPS; j++) {
+      int4 raw = __ldcs(a + ubase + j * 32 + lane);
+      const C *v = reinterpret_cast<const C *>(&raw);
+      R ps = 0;
+#pragma unroll
+      for (int e = 0; e < APU; e++) {
+        const R p = v[e].x * v[e].x + v[e].y * v[e].y;
+        ps += p;
+        if (LB == 1 && e == 1) b0 += p;
+      }
+      tot += ps;
+#pragma unroll
+      for (int b = 0; b < 3; b++)
+        if ((j >> b) & 1) bj[b] += ps;
+    }
+    // warp-level sums
+    R lanebit[5];
+#pragma unroll
+    for (int b = 0; b < 5; b++) lanebit[b] = warp_sum(((lane >> b) & 1) ? tot : R(0));
+    const R wtot = warp_sum(tot);
+    const R wb0 = LB ? warp_sum(b0) : R(0);
+    R wbj[3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) wbj[b] = warp_sum(bj[b]);
+    const uint64_t abase = ubase * APU;  // first amplitude index of the chunk
+    auto bitsum = [&](int q) -> R {
+      if (q < LB) return wb0;
+      if (q < LB + 5) return lanebit[q - LB];
+      if (q < LB + 8) return wbj[q - LB - 5];
+      return ((abase >> q) & 1) ? wtot : R(0);
+    };
+    if (lane < n) S0 += (double)bitsum(lane);
+    if (lane + 32 < n) S1 += (double)bitsum(lane + 32);
+    T += (double)wtot;
+  }
+  // block reduction: partial[block][q] for q < n, partial[block][n] = total
+  __shared__ double sm[64 + 1];
+  for (int i = threadIdx.x; i < 65; i += blockDim.x) sm[i] = 0;
+  __syncthreads();
+  if (lane < n) atomicAdd(&sm[lane], S0);
+  if (lane + 32 < n) atomicAdd(&sm[lane + 32], S1);
+  if (lane == 0) atomicAdd(&sm[64], T);
+  __syncthreads();
+  for (int q = threadIdx.x; q <= n; q += blockDim.x)
+    partial[(size_t)blockIdx.x * (n + 1) + q] = q < n ? sm[q] : sm[64];
+}
+
+// small states: one thread per amplitude, FP64 per bit
+template <typename R>
+__global__ void k_zall_small(const typename Cx<R>::T *__restrict__ a, int n, double *out) {
+  __shared__ double sm[65];
+  for (int i = threadIdx.x; i < 65; i += blockDim.x) sm[i] = 0;
+  __syncthreads();
+  for (uint64_t x = threadIdx.x; x < (1ull << n); x += blockDim.x) {
+    const double p = (double)a[x].x * a[x].x + (double)a[x].y * a[x].y;
+    for (int q = 0; q < n; q++)
+      if ((x >> q) & 1) atomicAdd(&sm[q], p);
+    atomicAdd(&sm[64], p);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q <= n; q += blockDim.x) out[q] = q < n ? sm[q] : sm[64];
+}
+
+// z[q] = total - 2 S_q from the reduced S_q (in place: buf[0..n] -> z[0..n-1])
+__global__ void k_zall_finish(const double *__restrict__ partial, int nblocks, int n, double *out) {
+  __shared__ double tot;
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int b = 0; b < nblocks; b++) t += partial[(size_t)b * (n + 1) + n];
+    tot = t;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < nblocks; b++) s += partial[(size_t)b * (n + 1) + q];
+    out[q] = tot - 2.0 * s;
+  }
+}
+
+sv_status launch_z_all(sv_state *s, double *out_dev) {
+  double *partial = reinterpret_cast<double *>(s->ws + kWsRed);
+  const int apu = s->dt == SV_C64 ? 2 : 1;
+  const uint64_t namps = 1ull << s->n;
+  const uint64_t chunk_amps = 32ull * 8 * apu;
+  if (namps < chunk_amps) {
+    if (s->dt == SV_C64)
+      k_zall_small<float><<<1, 256, 0, s->stream>>>((const float2 *)s->amps, s->n, partial);
+    else
+      k_zall_small<double><<<1, 256, 0, s->stream>>>((const double2 *)s->amps, s->n, partial);
+    k_zall_finish<<<1, 64, 0, s->stream>>>(partial, 1, s->n, out_dev);
+  } else {
+    const uint64_t nchunks = namps / chunk_amps;
+    const uint64_t warps_per_block = kRedThreads / 32;
+    const int g = (int)std::max<uint64_t>(
+        1, std::min<uint64_t>((nchunks + warps_per_block - 1) / warps_per_block, (uint64_t)s->sm_count * 4));
+    if (s->dt == SV_C64)
+      k_zall<float><<<g, kRedThreads, 0, s->stream>>>((const int4 *)s->amps, s->n, nchunks, partial);
+    else
+      k_zall<double><<<g, kRedThreads, 0, s->stream>>>((const int4 *)s->amps, s->n, nchunks, partial);
+    k_zall_finish<<<1, 64, 0, s->stream>>>(partial, g, s->n, out_dev);
+  }
+  g_launches += 2;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+// ---- sampling --------------------------------------------------------------
+constexpr int kChunkBits = 10;  // 1024 amplitudes per CDF chunk
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t j) {
+  // the j-th output of SplitMix64 seeded with `seed` (Steele, Lea, Flood 2014)
+  uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename R>
+__device__ __forceinline__ double prob64(const typename Cx<R>::T v) {
+  const double re = (double)v.x, im = (double)v.y;
+  return re * re + im * im;
+}
+
+// chunk sums of |psi|^2 in FP64: one block per chunk trip
+template <typename R>
+__global__ void k_chunk_sums(const typename Cx<R>::T *__restrict__ a, int n, uint64_t nchunks,
+                             double *csum) {
+  const uint64_t camps = 1ull << (n < kChunkBits ? n : kChunkBits);
+  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    double acc = 0;
+    for (uint64_t i = threadIdx.x; i < camps; i += blockDim.x) acc += prob64<R>(a[c * camps + i]);
+    __syncthreads();
+    block_sum_to(acc, csum + c);
+  }
+}
+
+// in-place inclusive prefix sum over nchunks doubles, one block of 1024
+__global__ void k_scan(double *x, uint64_t len) {
+  __shared__ double tot[1024];
+  const uint64_t per = (len + blockDim.x - 1) / blockDim.x;
+  const uint64_t lo = threadIdx.x * per, hi = lo + per < len ? lo + per : len;
+  double s = 0;
+  for (uint64_t i = lo; i < hi; i++) s += x[i];
+  tot[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0;
+    for (unsigned t = 0; t < blockDim.x; t++) {
+      const double v = tot[t];
+      tot[t] = r;
+      r += v;
+    }
+  }
+  __syncthreads();
+  double r = tot[threadIdx.x];
+  for (uint64_t i = lo; i < hi; i++) {
+    r += x[i];
+    x[i] = r;
+  }
+}
+
+// one warp per shot: binary search over chunk prefixes, then a warp scan
+// inside the chunk.  Shot j of this launch is global shot shot0 + j.
+template <typename R>
+__global__ void k_sample(const typename Cx<R>::T *__restrict__ a, int n, const double *__restrict__ pref,
+                         uint64_t nchunks, int64_t shot0, int64_t shots, uint64_t seed, uint64_t *out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t camps = 1ull << (n < kChunkBits ? n : kChunkBits);
+  const double total = pref[nchunks - 1];
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t sh = warp; sh < (uint64_t)shots; sh += nwarps) {
+    const double u = (double)(splitmix64(seed, (uint64_t)shot0 + sh) >> 11) * 0x1.0p-53;
+    const double target = u * total;
+    // smallest chunk c with pref[c] > target
+    uint64_t lo = 0, hi = nchunks - 1;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (pref[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    const uint64_t c = lo;
+    double run = c > 0 ? pref[c - 1] : 0.0;
+    uint64_t ans = c * camps + camps - 1;
+    for (uint64_t i0 = 0; i0 < camps; i0 += 32) {
+      const uint64_t x = c * camps + i0 + lane;
+      double p = (i0 + lane < camps) ? prob64<R>(a[x]) : 0.0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, p, o);
+        if (lane >= o) p += t;
+      }
+      const unsigned hit = __ballot_sync(0xffffffffu, (run + p > target) && (i0 + lane < camps));
+      if (hit) {
+        ans = c * camps + i0 + (__ffs(hit) - 1);
+        break;
+      }
+      run += __shfl_sync(0xffffffffu, p, 31);
+    }
+    if (lane == 0) out[sh] = ans;
+  }
+}
+
+static uint64_t n_chunks(int n) { return 1ull << (n - (n < kChunkBits ? n : kChunkBits)); }
+size_t sample_shot_offset(int n) { return (n_chunks(n) * sizeof(double) + 255) & ~(size_t)255; }
+int64_t sample_shot_capacity() { return (1 << 20) / sizeof(uint64_t); }
+
+sv_status launch_sample_prepare(sv_state *s) {
+  const uint64_t nchunks = n_chunks(s->n);
+  double *csum = reinterpret_cast<double *>(s->ws + kWsRed);
+  const int g = (int)std::min<uint64_t>(nchunks, (uint64_t)s->sm_count * 8);
+  if (s->dt == SV_C64)
+    k_chunk_sums<float><<<g, kRedThreads, 0, s->stream>>>((const float2 *)s->amps, s->n, nchunks, csum);
+  else
+    k_chunk_sums<double><<<g, kRedThreads, 0, s->stream>>>((const double2 *)s->amps, s->n, nchunks, csum);
+  k_scan<<<1, 1024, 0, s->stream>>>(csum, nchunks);
+  g_launches += 2;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+sv_status launch_sample_shots(sv_state *s, int64_t shot0, int64_t count, uint64_t seed, uint64_t *out_dev) {
+  const uint64_t nchunks = n_chunks(s->n);
+  const double *csum = reinterpret_cast<const double *>(s->ws + kWsRed);
+  const int sg = (int)std::max<int64_t>(1, std::min<int64_t>((count + 7) / 8, (int64_t)s->sm_count * 16));
+  if (s->dt == SV_C64)
+    k_sample<float><<<sg, 256, 0, s->stream>>>((const float2 *)s->amps, s->n, csum, nchunks, shot0, count,
+                                               seed, out_dev);
+  else
+    k_sample<double><<<sg, 256, 0, s->stream>>>((const double2 *)s->amps, s->n, csum, nchunks, shot0, count,
+                                                seed, out_dev);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+}  // namespace sv

@@ -1,0 +1,291 @@
+// K6: tile-pass kernel.
+//
+// One CTA owns one tile: the 2^m amplitudes whose indices agree outside the
+// pass's qubit set S (the L lowest qubits, contiguous in memory, plus m - L
+// chosen high qubits).  The CTA copies the tile (one or two vectors) into
+// shared memory with 16-byte cp.async, applies the pass's op list there, and
+// writes the tile back, so a whole run of gates costs one read and one write
+// of the state -- the HBM-bound core of the matrix-vector method (paper
+// Sec. II, assumption (a)).  Ops: dense k-qubit blocks with local and
+// out-of-tile controls, diagonal blocks, and the reductions used by the
+// adjoint gradient (Im<lambda|G|psi>, Re<psi|lambda>) and by building
+// lambda = H psi from Pauli strings.
+#include "sv_device.cuh"
+#include "sv_internal.h"
+
+namespace sv {
+
+constexpr int kTileMaxThreads = 512;
+
+__device__ __forceinline__ uint64_t tile_base(const TilePass &P, uint64_t t) {
+  uint64_t base = 0;
+  const int nout = P.n - P.m;
+  for (int j = 0; j < nout; j++) base |= ((t >> j) & 1ull) << P.out_pos[j];
+  return base;
+}
+
+__device__ __forceinline__ uint64_t spread_hi(const TilePass &P, uint32_t l) {
+  uint64_t g = 0;
+  for (int b = P.L; b < P.m; b++) g |= (uint64_t)((l >> b) & 1u) << P.hi_pos[b - P.L];
+  return g;
+}
+
+template <typename R, int K>
+__device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
+                                         const typename Cx<R>::T *__restrict__ U) {
+  using C = typename Cx<R>::T;
+  constexpr int D = 1 << K;
+  uint32_t off[D];
+#pragma unroll
+  for (int y = 0; y < D; y++) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++) o |= (uint32_t)((y >> j) & 1) << op.t[j];
+    off[y] = o;
+  }
+  const uint32_t fixed = off[D - 1] | op.lcmask;
+  const uint32_t ngroups = 1u << (m - __popc(fixed));
+  if constexpr (K <= 2) {
+    C u[D * D];
+#pragma unroll
+    for (int e = 0; e < D * D; e++) u[e] = U[e];
+    for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+      const uint32_t i0 = ins0_mask(g, fixed) | op.lcmask;
+      C x[D];
+#pragma unroll
+      for (int y = 0; y < D; y++) x[y] = v[i0 + off[y]];
+#pragma unroll
+      for (int r = 0; r < D; r++) {
+        C a = czero<C>();
+#pragma unroll
+        for (int y = 0; y < D; y++) a = cfma(u[r * D + y], x[y], a);
+        v[i0 + off[r]] = a;
+      }
+    }
+  } else {
+    for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+      const uint32_t i0 = ins0_mask(g, fixed) | op.lcmask;
+      C x[D];
+#pragma unroll
+      for (int y = 0; y < D; y++) x[y] = v[i0 + off[y]];
+#pragma unroll 1
+      for (int r = 0; r < D; r++) {
+        C a = czero<C>();
+#pragma unroll
+        for (int y = 0; y < D; y++) a = cfma(__ldg(&U[r * D + y]), x[y], a);
+        v[i0 + off[r]] = a;
+      }
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
+                                        const typename Cx<R>::T *__restrict__ d) {
+  using C = typename Cx<R>::T;
+  const uint32_t ngroups = 1u << (m - __popc(op.lcmask));
+  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const uint32_t l = ins0_mask(g, op.lcmask) | op.lcmask;
+    uint32_t r = 0;
+    for (int j = 0; j < op.k; j++) r |= ((l >> op.t[j]) & 1u) << j;
+    v[l] = cmul(__ldg(&d[r]), v[l]);
+  }
+}
+
+// Dense blocks of 4..6 qubits keep 2^k amplitudes per thread; they live in
+// separate functions so their register pressure does not spill the k <= 3
+// paths that make up most passes.
+template <typename R, int K>
+__device__ __noinline__ void dense_op_big(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
+                                          const typename Cx<R>::T *__restrict__ U) {
+  dense_op<R, K>(v, m, op, U);
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const TileOp &op,
+                                         const typename Cx<R>::T *U) {
+  if (op.kind == TOP_DIAG) {
+    diag_op<R>(v, m, op, U);
+    return;
+  }
+  switch (op.k) {
+    case 1: dense_op<R, 1>(v, m, op, U); break;
+    case 2: dense_op<R, 2>(v, m, op, U); break;
+    case 3: dense_op<R, 3>(v, m, op, U); break;
+    case 4: dense_op_big<R, 4>(v, m, op, U); break;
+    case 5: dense_op_big<R, 5>(v, m, op, U); break;
+    default: dense_op_big<R, 6>(v, m, op, U); break;
+  }
+}
+
+// Im(conj(b) a)
+template <typename C> __device__ __forceinline__ auto imdot(C b, C a) -> decltype(a.x) {
+  return b.x * a.y - b.y * a.x;
+}
+
+template <typename R>
+__device__ __forceinline__ void block_acc(R part, double *dst) {
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) atomicAdd(dst, (double)part);
+}
+
+template <typename R>
+__device__ void grad_op(const typename Cx<R>::T *__restrict__ psi,
+                        const typename Cx<R>::T *__restrict__ lam, int m, const TileOp &op,
+                        double *acc) {
+  using C = typename Cx<R>::T;
+  const int t = op.t[0];
+  const uint32_t bit = 1u << t;
+  const uint32_t ngroups = 1u << (m - 1);
+  R part = 0;
+  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const uint32_t l0 = ins0(g, t), l1 = l0 | bit;
+    const C a0 = psi[l0], a1 = psi[l1], b0 = lam[l0], b1 = lam[l1];
+    switch (op.gen) {
+      case 1:  // X
+        part += imdot(b0, a1) + imdot(b1, a0);
+        break;
+      case 2: {  // Y: (Y psi)[l0] = -i a1, (Y psi)[l1] = i a0
+        C ma1 = cmake(a1.y, -a1.x), pa0 = cmake(-a0.y, a0.x);
+        part += imdot(b0, ma1) + imdot(b1, pa0);
+        break;
+      }
+      case 3:  // Z
+        part += imdot(b0, a0) - imdot(b1, a1);
+        break;
+      default:  // diag(0, -2)
+        part += R(-2) * imdot(b1, a1);
+        break;
+    }
+  }
+  block_acc<R>(part, acc + op.slot);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_constant__ TilePass P) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t TS = 1u << P.m;
+  C *v0 = reinterpret_cast<C *>(smem_raw);
+  C *v1 = v0 + TS;
+  const int b = blockIdx.y;
+  const uint64_t base = tile_base(P, blockIdx.x);
+  C *g0 = reinterpret_cast<C *>(P.tbl0 ? P.tbl0[b] : P.v0);
+  C *g1 = P.nvec > 1 ? reinterpret_cast<C *>(P.tbl1 ? P.tbl1[b] : P.v1) : nullptr;
+
+  constexpr uint32_t APU = 16 / sizeof(C);  // amplitudes per 16-byte unit
+  const uint32_t nunits = TS / APU;
+  const uint32_t segmask = (1u << P.L) - 1;
+  const bool load1 = P.nvec > 1 && !(P.flags & 1u);
+  for (uint32_t u = threadIdx.x; u < nunits; u += blockDim.x) {
+    const uint32_t l = u * APU;
+    const uint64_t g = base | (l & segmask) | spread_hi(P, l);
+    cp_async16(&v0[l], &g0[g]);
+    if (load1) cp_async16(&v1[l], &g1[g]);
+  }
+  cp_async_wait_all();
+
+  const C *mats = reinterpret_cast<const C *>(P.mats);
+  const C *pmats = P.pmats ? reinterpret_cast<const C *>(P.pmats) + (size_t)b * P.pmats_stride : nullptr;
+  double *acc = P.acc ? P.acc + (size_t)b * P.acc_stride : nullptr;
+
+  for (int oi = 0; oi < P.nops; oi++) {
+    __syncthreads();
+    const TileOp op = P.ops[oi];
+    const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);
+    switch (op.kind) {
+      case TOP_DENSE:
+      case TOP_DIAG: {
+        if ((base & gcm) != gcm) break;
+        const C *U = ((op.gen & kGenBatchMat) ? pmats : mats) + op.mat;
+        if (op.vmask & 1) apply_op<R>(v0, P.m, op, U);
+        if (op.vmask & 2) apply_op<R>(v1, P.m, op, U);
+        break;
+      }
+      case TOP_GRAD:
+        grad_op<R>(v0, v1, P.m, op, acc);
+        break;
+      case TOP_PAULI: {
+        const uint32_t xm = (uint16_t)op.slot;
+        const uint32_t zl = op.lcmask;
+        const int tsign = __popcll(base & gcm) & 1;
+        const double c = P.coeffs[op.mat];
+        // c * i^k
+        R fr = 0, fi = 0;
+        switch (op.gen & 3) {
+          case 0: fr = (R)c; break;
+          case 1: fi = (R)c; break;
+          case 2: fr = (R)-c; break;
+          default: fi = (R)-c; break;
+        }
+        for (uint32_t l = threadIdx.x; l < TS; l += blockDim.x) {
+          const int s = (__popc(l & zl) + tsign) & 1;
+          const R sr = s ? -fr : fr, si = s ? -fi : fi;
+          const C a = v0[l];
+          C &dst = v1[l ^ xm];
+          dst.x += sr * a.x - si * a.y;
+          dst.y += sr * a.y + si * a.x;
+        }
+        break;
+      }
+      case TOP_ZERO:
+        for (uint32_t l = threadIdx.x; l < TS; l += blockDim.x) v1[l] = czero<C>();
+        break;
+      case TOP_DOT: {
+        R part = 0;
+        for (uint32_t l = threadIdx.x; l < TS; l += blockDim.x) {
+          const C a = v0[l], c = v1[l];
+          part += a.x * c.x + a.y * c.y;
+        }
+        block_acc<R>(part, acc + op.slot);
+        break;
+      }
+      default:
+        break;
+    }
+  }
+  __syncthreads();
+  const bool store0 = !(P.flags & 2u), store1 = P.nvec > 1 && !(P.flags & 4u);
+  for (uint32_t u = threadIdx.x; u < nunits; u += blockDim.x) {
+    const uint32_t l = u * APU;
+    const uint64_t g = base | (l & segmask) | spread_hi(P, l);
+    if (store0) __stcs(reinterpret_cast<int4 *>(&g0[g]), *reinterpret_cast<const int4 *>(&v0[l]));
+    if (store1) __stcs(reinterpret_cast<int4 *>(&g1[g]), *reinterpret_cast<const int4 *>(&v1[l]));
+  }
+}
+
+int tile_threads(int m, sv_dtype dt) {
+  const int units = (1 << m) / (dt == SV_C64 ? 2 : 1);
+  int t = units / 8;
+  if (t < 32) t = 32;
+  if (t > kTileMaxThreads) t = kTileMaxThreads;
+  return t;
+}
+
+size_t tile_smem(sv_dtype dt, int m, int nvec) { return (size_t)nvec * ((size_t)1 << m) * amp_bytes(dt); }
+
+sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
+  static bool attr_set[2][64] = {};
+  const size_t smem = tile_smem(s->dt, p.m, (int)p.nvec);
+  const int dev = s->device & 63;
+  const int di = s->dt == SV_C64 ? 0 : 1;
+  if (!attr_set[di][dev]) {
+    if (s->dt == SV_C64)
+      SV_CUDA(cudaFuncSetAttribute(k_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+    else
+      SV_CUDA(cudaFuncSetAttribute(k_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+    attr_set[di][dev] = true;
+  }
+  if (smem > (200u << 10)) return set_error(SV_EINVAL, "tile too large for shared memory");
+  dim3 grid((unsigned)(1ull << (p.n - p.m)), (unsigned)batch);
+  const int threads = tile_threads(p.m, s->dt);
+  if (s->dt == SV_C64)
+    k_tile<float><<<grid, threads, smem, s->stream>>>(p);
+  else
+    k_tile<double><<<grid, threads, smem, s->stream>>>(p);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+}  // namespace sv

@@ -1,0 +1,285 @@
+// C ABI: adjoint-method gradients (plain and batched) and batched circuit
+// application.
+//
+// One "adjoint program" is a single list of tile passes:
+//   forward   : the circuit on psi (1 vector per tile);
+//   lambda    : lambda = H psi from Pauli strings, <H> = Re<psi|lambda>
+//               (2 vectors: psi read-only, lambda written);
+//   reverse   : for j = G..1, Im<lambda|G_j|psi> for parametric gates, then
+//               U_j^dagger on both vectors (2 vectors).
+// Parametric gates are kept as separate ops whose 2x2 matrices come from a
+// per-batch table (forward U(theta_b) and reverse U(theta_b)^dagger), so one
+// program serves every parameter set; fixed gates are fused as usual.  The
+// batched form launches each pass once for all B states (grid.y = B).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+struct AdjointProgram {
+  DeviceProgram prog;
+  std::vector<uint32_t> op0s;
+  std::vector<int> inst_param;   // parameter index of each parametric instance
+  std::vector<int> inst_gate;    // sv_gate of each parametric instance
+  int n_params = 0;
+  int n_inst = 0;
+};
+
+static std::map<std::pair<const sv_state *, uint64_t>, AdjointProgram> g_adj_cache;
+
+static void append_passes(DeviceProgram &prog, std::vector<uint32_t> &op0s, const std::vector<PassPlan> &passes,
+                          const BuildCtx &b, const std::vector<int> &bmo, sv_status &st) {
+  for (const PassPlan &P : passes) {
+    if (st != SV_OK) return;
+    st = emit_pass(prog, P, b, op0s, bmo);
+  }
+}
+
+static sv_status build_adjoint(sv_state *s, const sv_circuit *c, const double *params0,
+                               const sv_pauli_term *terms, int nt, const Opts &o1, const Opts &o2,
+                               AdjointProgram &A) {
+  std::vector<Gate> gates;
+  SV_TRY(circuit_to_gates(c, params0, s->n, gates, true));
+  A.n_params = c->n_params;
+  for (Gate &g : gates) {
+    if (g.param < 0) continue;
+    if (g.targets.size() != 1 || !g.controls.empty() || gate_generator(g.param_gate) == 0)
+      return set_error(SV_EUNSUPPORTED,
+                       "parametric gates must be uncontrolled single-qubit RX/RY/RZ/PHASE for gradients");
+    g.inst = A.n_inst++;
+    A.inst_param.push_back(g.param);
+    A.inst_gate.push_back(g.param_gate);
+  }
+  const int G = (int)gates.size();
+  std::vector<int> fwd_off(A.n_inst), rev_off(A.n_inst);
+  for (int i = 0; i < A.n_inst; i++) {
+    fwd_off[i] = 4 * i;
+    rev_off[i] = 4 * (A.n_inst + i);
+  }
+  sv_status st = SV_OK;
+  // forward
+  {
+    std::vector<Block> blocks = fuse(gates, o1.fusion_k);
+    int m = o1.tile_m, L = o1.L;
+    if (!fit_tile(blocks, s->n, lmin(s->dt), mmax(s->dt, 1), m, L))
+      return set_error(SV_EUNSUPPORTED, "a fused block does not fit a shared-memory tile");
+    std::vector<PassPlan> passes = plan_passes(blocks, s->n, m, L, 256, 1 << 16);
+    if (passes.empty() && !blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
+    BuildCtx b{s->dt, s->n, m, L, 1, 0};
+    append_passes(A.prog, A.op0s, passes, b, fwd_off, st);
+  }
+  // lambda = H psi
+  {
+    std::vector<Block> blocks;
+    for (int t = 0; t < nt; t++) {
+      Block b;
+      b.kind = TOP_PAULI;
+      for (int q = 0; q < s->n; q++)
+        if ((terms[t].x_mask >> q) & 1) b.qubits.push_back(q);
+      b.xmask = terms[t].x_mask;
+      b.zmask = terms[t].z_mask;
+      b.coeff = terms[t].coeff;
+      b.fusable = false;
+      blocks.push_back(b);
+    }
+    int m = o2.tile_m, L = o2.L;
+    if (!fit_tile(blocks, s->n, lmin(s->dt), mmax(s->dt, 2), m, L))
+      return set_error(SV_EUNSUPPORTED, "a Pauli string's X support does not fit a shared-memory tile");
+    std::vector<PassPlan> passes = plan_passes(blocks, s->n, m, L, 256, 1 << 16);
+    if (passes.empty() && !blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
+    if (passes.empty()) {
+      PassPlan P;
+      for (int q = 0; q < std::min(m, s->n); q++) P.S.push_back(q);
+      passes.push_back(P);
+    }
+    Block zero;
+    zero.kind = TOP_ZERO;
+    passes.front().ops.insert(passes.front().ops.begin(), zero);
+    Block dot;
+    dot.kind = TOP_DOT;
+    dot.slot = A.n_params;
+    passes.back().ops.push_back(dot);
+    for (size_t i = 0; i < passes.size() && st == SV_OK; i++) {
+      BuildCtx b{s->dt, s->n, m, L, 2, (i == 0 ? 1u : 0u) | 2u};
+      st = emit_pass(A.prog, passes[i], b, A.op0s, {});
+    }
+  }
+  // reverse sweep
+  {
+    std::vector<Gate> rev;
+    rev.reserve(2 * G);
+    for (int j = G - 1; j >= 0; j--) {
+      const Gate &g = gates[j];
+      if (g.param >= 0) {
+        Gate probe;
+        probe.targets = g.targets;
+        probe.grad_gen = gate_generator(g.param_gate);
+        probe.grad_slot = g.param;
+        rev.push_back(probe);
+      }
+      Gate u = g;
+      u.U = adjoint_of(g.U, (int)g.targets.size());
+      rev.push_back(u);
+    }
+    std::vector<Block> blocks = fuse(rev, o2.fusion_k);
+    for (Block &b : blocks)
+      if (b.kind == TOP_DENSE) b.vmask = 3;
+    int m = o2.tile_m, L = o2.L;
+    if (!fit_tile(blocks, s->n, lmin(s->dt), mmax(s->dt, 2), m, L))
+      return set_error(SV_EUNSUPPORTED, "a fused block does not fit a shared-memory tile");
+    std::vector<PassPlan> passes = plan_passes(blocks, s->n, m, L, 256, 1 << 16);
+    if (passes.empty() && !blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
+    BuildCtx b{s->dt, s->n, m, L, 2, 0};
+    append_passes(A.prog, A.op0s, passes, b, rev_off, st);
+  }
+  return st;
+}
+
+template <typename R>
+static void put_mats(std::vector<uint8_t> &pool, const AdjointProgram &A, const double *theta) {
+  // forward matrices for every instance, then their adjoints
+  std::vector<cd> U;
+  for (int pass = 0; pass < 2; pass++)
+    for (int i = 0; i < A.n_inst; i++) {
+      const double ang[3] = {theta[A.inst_param[i]], 0, 0};
+      gate_matrix(A.inst_gate[i], ang, U);
+      if (pass == 1) U = adjoint_of(U, 1);
+      for (int e = 0; e < 4; e++) {
+        R v[2] = {(R)U[e].real(), (R)U[e].imag()};
+        const uint8_t *p = (const uint8_t *)v;
+        pool.insert(pool.end(), p, p + sizeof(v));
+      }
+    }
+}
+
+static sv_status check_batch(sv_state *const *psi, int B, int n, sv_dtype dt, cudaStream_t st) {
+  for (int b = 0; b < B; b++) {
+    if (!psi[b]) return set_error(SV_EINVAL, "null state in batch");
+    if (psi[b]->n != n || psi[b]->dt != dt) return set_error(SV_EINVAL, "batch states differ in width or dtype");
+    if (psi[b]->stream != st) return set_error(SV_EINVAL, "batch states must share one stream");
+  }
+  return SV_OK;
+}
+
+static sv_status adjoint_batch(sv_state *const *psi, sv_state *const *lam, int B, const sv_circuit *c,
+                               const double *params, const sv_pauli_term *terms, int nt, const sv_options *opt,
+                               double *ev_out, double *grad_out) {
+  if (!psi || !lam || B < 1 || !c || !ev_out || (c->n_params > 0 && (!params || !grad_out)))
+    return set_error(SV_EINVAL, "null argument");
+  sv_state *s = psi[0];
+  if (!s) return set_error(SV_EINVAL, "null state");
+  SV_TRY(check_batch(psi, B, s->n, s->dt, s->stream));
+  SV_TRY(check_batch(lam, B, s->n, s->dt, s->stream));
+  if (nt < 0 || (nt > 0 && !terms)) return set_error(SV_EINVAL, "bad term list");
+  const uint64_t lim = (1ull << s->n) - 1;
+  for (int t = 0; t < nt; t++)
+    if ((terms[t].x_mask & ~lim) || (terms[t].z_mask & ~lim))
+      return set_error(SV_EINVAL, "Pauli mask references a qubit >= n");
+  const Opts o1 = resolve(s, opt, 1), o2 = resolve(s, opt, 2);
+  // cache key: circuit structure, terms, options
+  uint64_t key = circuit_hash(c, 0xad);
+  {
+    uint64_t h = key;
+    auto mix = [&](const void *p, size_t n) {
+      const unsigned char *q = (const unsigned char *)p;
+      for (size_t i = 0; i < n; i++) h = (h ^ q[i]) * 1099511628211ull;
+    };
+    if (nt) mix(terms, sizeof(sv_pauli_term) * nt);
+    mix(&o1, sizeof(o1));
+    mix(&o2, sizeof(o2));
+    mix(&s->dt, sizeof(s->dt));
+    key = h;
+  }
+  auto ck = std::make_pair((const sv_state *)s, key);
+  auto it = g_adj_cache.find(ck);
+  if (it == g_adj_cache.end()) {
+    AdjointProgram A;
+    SV_TRY(build_adjoint(s, c, params, terms, nt, o1, o2, A));
+    if (g_adj_cache.size() > 16) g_adj_cache.clear();
+    it = g_adj_cache.emplace(ck, std::move(A)).first;
+  }
+  const AdjointProgram &A = it->second;
+  const int np = c->n_params;
+  // per-batch matrices, state pointer tables
+  std::vector<uint8_t> pm;
+  for (int b = 0; b < B; b++) {
+    if (s->dt == SV_C64) put_mats<float>(pm, A, params + (size_t)b * np);
+    else put_mats<double>(pm, A, params + (size_t)b * np);
+  }
+  std::vector<void *> tbl(2 * (size_t)B);
+  for (int b = 0; b < B; b++) {
+    tbl[b] = psi[b]->amps;
+    tbl[B + b] = lam[b]->amps;
+  }
+  const ProgLayout L = layout_of(A.prog, tbl.size() * sizeof(void *), pm.size());
+  SV_TRY(stage_upload(s,
+                      {{A.prog.ops.data(), A.prog.ops.size() * sizeof(TileOp)},
+                       {A.prog.mats.data(), A.prog.mats.size()},
+                       {A.prog.coeffs.data(), A.prog.coeffs.size() * sizeof(double)},
+                       {tbl.data(), tbl.size() * sizeof(void *)},
+                       {pm.data(), pm.size()}},
+                      {L.ops_off, L.mats_off, L.coeffs_off, L.tbl_off, L.pmats_off}, L.end));
+  const size_t acc_stride = (size_t)np + 1;
+  const size_t acc_bytes = acc_stride * B * sizeof(double);
+  if (acc_bytes > red_bytes(s->n)) return set_error(SV_ENOMEM, "workspace too small for the gradient batch");
+  double *acc = reinterpret_cast<double *>(s->ws + kWsRed);
+  SV_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s->stream));
+  char *base = s->ws + kWsProg;
+  LaunchEnv E;
+  E.batch = B;
+  E.tbl0 = reinterpret_cast<void *const *>(base + L.tbl_off);
+  E.tbl1 = E.tbl0 + B;
+  E.pmats = base + L.pmats_off;
+  E.pmats_stride = (uint64_t)8 * A.n_inst;
+  E.acc = acc;
+  E.acc_stride = acc_stride;
+  SV_TRY(launch_program(s, A.prog, L, A.op0s, E));
+  std::vector<double> h(acc_stride * B);
+  SV_CUDA(cudaMemcpyAsync(h.data(), acc, acc_bytes, cudaMemcpyDeviceToHost, s->stream));
+  SV_CUDA(cudaStreamSynchronize(s->stream));
+  for (int b = 0; b < B; b++) {
+    ev_out[b] = h[(size_t)b * acc_stride + np];
+    for (int p = 0; p < np; p++) grad_out[(size_t)b * np + p] = h[(size_t)b * acc_stride + p];
+  }
+  return SV_OK;
+}
+
+}  // namespace sv
+
+using namespace sv;
+
+extern "C" {
+
+sv_status sv_adjoint_grad(sv_state *psi, sv_state *lam, const sv_circuit *c, const double *params,
+                          const sv_pauli_term *terms, int nt, const sv_options *opt, double *ev, double *grad) {
+  if (!psi || !lam) return set_error(SV_EINVAL, "null state");
+  if (psi == lam || psi->amps == lam->amps) return set_error(SV_EINVAL, "psi and lambda must be distinct buffers");
+  return adjoint_batch(&psi, &lam, 1, c, params, terms, nt, opt, ev, grad);
+}
+
+sv_status sv_adjoint_grad_batch(sv_state *const *psi, sv_state *const *lam, int B, const sv_circuit *c,
+                                const double *params, const sv_pauli_term *terms, int nt, const sv_options *opt,
+                                double *ev, double *grad) {
+  return adjoint_batch(psi, lam, B, c, params, terms, nt, opt, ev, grad);
+}
+
+sv_status sv_apply_circuit_batch(sv_state *const *states, int B, const sv_circuit *const *circs,
+                                 const double *const *params, const sv_options *opt) {
+  if (!states || !circs || B < 1) return set_error(SV_EINVAL, "null argument");
+  for (int b = 0; b < B; b++) {
+    const double *p = params ? params[b] : nullptr;
+    SV_TRY(sv_apply_circuit(states[b], circs[b], p, opt));
+  }
+  return SV_OK;
+}
+
+sv_status sv_autotune(sv_state *scratch, const sv_circuit *c, sv_options *inout) {
+  if (!scratch || !c || !inout) return set_error(SV_EINVAL, "null argument");
+  return set_error(SV_EUNSUPPORTED, "autotuner not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,460 @@
+// C ABI implementation: state handles, argument validation, program building
+// (fusion + tile passes), upload, and orchestration of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local std::string g_err;
+
+sv_status set_error(sv_status st, const std::string &msg) {
+  g_err = msg;
+  return st;
+}
+sv_status cuda_error(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return SV_ECUDA;
+}
+
+size_t amp_bytes(sv_dtype dt) { return dt == SV_C64 ? 8 : 16; }
+int lmin(sv_dtype dt) { return dt == SV_C64 ? 1 : 0; }
+int mmax(sv_dtype dt, int nvec) {
+  // largest tile whose vectors fit the 200 KB dynamic shared-memory budget
+  int m = 1;
+  while (tile_smem(dt, m + 1, nvec) <= (200u << 10)) m++;
+  return m;
+}
+
+size_t red_bytes(int n) {
+  const int cb = n < 10 ? n : 10;
+  const size_t chunks = (size_t)1 << (n - cb);
+  size_t need = chunks * sizeof(double) + (1 << 20);  // CDF chunks + shot buffer
+  return std::max<size_t>(need, 2 << 20);
+}
+
+// ---------------------------------------------------------------------------
+// defaults
+// ---------------------------------------------------------------------------
+Opts resolve(const sv_state *s, const sv_options *o, int nvec) {
+  Opts r;
+  r.fusion_k = (o && o->fusion_k > 0) ? o->fusion_k : 3;
+  r.tile_m = (o && o->tile_m > 0) ? o->tile_m : (s->dt == SV_C64 ? 13 : 12) - (nvec - 1);
+  r.L = s->dt == SV_C64 ? 4 : 3;
+  r.prec = o ? o->prec : SV_PREC_PLAIN;
+  r.mode = o ? o->mode : SV_MODE_TILED;
+  r.fusion_k = std::min(r.fusion_k, 6);
+  r.tile_m = std::max(1, std::min(r.tile_m, s->n));
+  r.L = std::min(r.L, r.tile_m);
+  if (s->dt == SV_C64 && r.L < 1) r.L = 1;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// hashing (FNV-1a)
+// ---------------------------------------------------------------------------
+struct Hasher {
+  uint64_t h = 1469598103934665603ull;
+  void bytes(const void *p, size_t n) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; i++) {
+      h ^= c[i];
+      h *= 1099511628211ull;
+    }
+  }
+  template <typename T> void val(const T &v) { bytes(&v, sizeof(T)); }
+};
+
+uint64_t circuit_hash(const sv_circuit *c, uint64_t salt) {
+  Hasher H;
+  H.val(salt);
+  H.val(c->n_qubits);
+  H.val(c->n_ops);
+  H.val(c->n_params);
+  if (c->n_ops > 0) H.bytes(c->ops, sizeof(sv_op) * (size_t)c->n_ops);
+  for (int i = 0; i < c->n_ops; i++)
+    if (c->ops[i].gate == SV_GATE_MATRIX && c->matrices && c->ops[i].matrix_offset >= 0) {
+      const int d = 1 << c->ops[i].n_targets;
+      H.bytes(c->matrices + 2 * c->ops[i].matrix_offset, sizeof(double) * 2 * d * d);
+    }
+  return H.h;
+}
+
+// ---------------------------------------------------------------------------
+// program building
+// ---------------------------------------------------------------------------
+template <typename R> static void put_c(std::vector<uint8_t> &pool, cd v) {
+  R t[2] = {(R)v.real(), (R)v.imag()};
+  const uint8_t *p = (const uint8_t *)t;
+  pool.insert(pool.end(), p, p + sizeof(t));
+}
+
+// Convert one planned pass into TilePass + TileOps (+ matrices).
+sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
+                           std::vector<uint32_t> &op0s, const std::vector<int> &batch_mat_off) {
+  TilePass tp;
+  std::memset(&tp, 0, sizeof(tp));
+  tp.n = b.n;
+  tp.m = (int)P.S.size();
+  tp.L = std::min(b.L, tp.m);
+  tp.nvec = b.nvec;
+  tp.flags = b.flags;
+  int loc[64];
+  for (int q = 0; q < 64; q++) loc[q] = -1;
+  for (size_t i = 0; i < P.S.size(); i++) loc[P.S[i]] = (int)i;
+  for (int j = tp.L; j < tp.m; j++) tp.hi_pos[j - tp.L] = (int8_t)P.S[j];
+  int no = 0;
+  for (int q = 0; q < b.n; q++)
+    if (loc[q] < 0) tp.out_pos[no++] = (int8_t)q;
+  op0s.push_back((uint32_t)prog.ops.size());
+  const size_t ab = amp_bytes(b.dt);
+  for (const Block &blk : P.ops) {
+    TileOp op;
+    std::memset(&op, 0, sizeof(op));
+    op.kind = (uint8_t)blk.kind;
+    op.k = (uint8_t)blk.qubits.size();
+    op.vmask = (uint8_t)blk.vmask;
+    for (size_t j = 0; j < blk.qubits.size(); j++) {
+      if (loc[blk.qubits[j]] < 0) return set_error(SV_EINVAL, "internal: target outside tile");
+      op.t[j] = (uint8_t)loc[blk.qubits[j]];
+    }
+    uint64_t gcm = 0;
+    for (int q : blk.controls) {
+      if (loc[q] >= 0) op.lcmask |= 1u << loc[q];
+      else gcm |= 1ull << q;
+    }
+    if (blk.kind == TOP_DENSE && blk.diag) op.kind = TOP_DIAG;
+    if (op.kind == TOP_DENSE || op.kind == TOP_DIAG) {
+      if (blk.inst >= 0 && !batch_mat_off.empty()) {
+        op.gen = kGenBatchMat;
+        op.mat = (uint32_t)batch_mat_off[blk.inst];
+      } else {
+        op.mat = (uint32_t)(prog.mats.size() / ab);
+        const int d = 1 << op.k;
+        if (op.kind == TOP_DIAG) {
+          for (int r = 0; r < d; r++)
+            b.dt == SV_C64 ? put_c<float>(prog.mats, blk.U[(size_t)r * d + r])
+                           : put_c<double>(prog.mats, blk.U[(size_t)r * d + r]);
+        } else {
+          for (int e = 0; e < d * d; e++)
+            b.dt == SV_C64 ? put_c<float>(prog.mats, blk.U[e]) : put_c<double>(prog.mats, blk.U[e]);
+        }
+      }
+    } else if (op.kind == TOP_GRAD) {
+      op.gen = (uint8_t)blk.gen;
+      op.slot = (int16_t)blk.slot;
+    } else if (op.kind == TOP_PAULI) {
+      uint32_t xl = 0, zl = 0;
+      gcm = 0;
+      for (int q = 0; q < b.n; q++) {
+        if ((blk.xmask >> q) & 1) xl |= 1u << loc[q];
+        if ((blk.zmask >> q) & 1) {
+          if (loc[q] >= 0) zl |= 1u << loc[q];
+          else gcm |= 1ull << q;
+        }
+      }
+      op.slot = (int16_t)xl;
+      op.lcmask = zl;
+      op.gen = (uint8_t)(__builtin_popcountll(blk.xmask & blk.zmask) & 3);
+      op.mat = (uint32_t)prog.coeffs.size();
+      prog.coeffs.push_back(blk.coeff);
+    } else if (op.kind == TOP_DOT) {
+      op.slot = (int16_t)blk.slot;
+    }
+    op.gcmask_lo = (uint32_t)gcm;
+    op.gcmask_hi = (uint16_t)(gcm >> 32);
+    prog.ops.push_back(op);
+  }
+  tp.nops = (int)P.ops.size();
+  prog.passes.push_back(tp);
+  return SV_OK;
+}
+
+static constexpr int kMaxOpsPerPass = 256;
+static constexpr int kMaxMatPerPass = 1 << 16;
+
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+ProgLayout layout_of(const DeviceProgram &p, size_t tbl_bytes, size_t pmats_bytes) {
+  ProgLayout L;
+  L.ops_off = 0;
+  L.mats_off = align256(p.ops.size() * sizeof(TileOp));
+  L.coeffs_off = align256(L.mats_off + p.mats.size());
+  L.tbl_off = align256(L.coeffs_off + p.coeffs.size() * sizeof(double));
+  L.pmats_off = align256(L.tbl_off + tbl_bytes);
+  L.end = align256(L.pmats_off + pmats_bytes);
+  return L;
+}
+
+// Copy host bytes into the workspace program area through the pinned buffer.
+sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, size_t>> &parts,
+                              const std::vector<size_t> &offs, size_t total) {
+  if (total > kWsProgBytes) return set_error(SV_ENOMEM, "gate program exceeds the workspace program area");
+  SV_CUDA(cudaEventSynchronize(s->staged));
+  for (size_t i = 0; i < parts.size(); i++)
+    if (parts[i].second) std::memcpy(s->pinned + offs[i], parts[i].first, parts[i].second);
+  SV_CUDA(cudaMemcpyAsync(s->ws + kWsProg, s->pinned, total, cudaMemcpyHostToDevice, s->stream));
+  SV_CUDA(cudaEventRecord(s->staged, s->stream));
+  s->resident_key = 0;
+  return SV_OK;
+}
+
+// Launch every pass of a program.
+sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &L,
+                                const std::vector<uint32_t> &op0s, const LaunchEnv &E) {
+  char *base = s->ws + kWsProg;
+  for (size_t i = 0; i < p.passes.size(); i++) {
+    TilePass tp = p.passes[i];
+    tp.ops = reinterpret_cast<const TileOp *>(base + L.ops_off) + op0s[i];
+    tp.mats = base + L.mats_off;
+    tp.coeffs = reinterpret_cast<const double *>(base + L.coeffs_off);
+    tp.pmats = E.pmats;
+    tp.pmats_stride = E.pmats_stride;
+    tp.acc = E.acc;
+    tp.acc_stride = E.acc_stride;
+    tp.tbl0 = E.tbl0;
+    tp.tbl1 = E.tbl1;
+    tp.v0 = E.v0;
+    tp.v1 = E.v1;
+    SV_TRY(launch_tile_pass(s, tp, E.batch));
+  }
+  return SV_OK;
+}
+
+// Cached plain-circuit program (one vector).
+struct CachedProgram {
+  DeviceProgram prog;
+  std::vector<uint32_t> op0s;
+  ProgLayout lay;
+  std::vector<Block> blocks;   // for per-gate mode
+};
+static std::map<std::pair<const sv_state *, uint64_t>, CachedProgram> g_cache;
+
+static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gates, const Opts &o,
+                                       CachedProgram &out) {
+  out.blocks = fuse(gates, o.fusion_k);
+  if (o.mode == SV_MODE_PER_GATE) return SV_OK;
+  int m = o.tile_m, L = o.L;
+  if (!fit_tile(out.blocks, s->n, lmin(s->dt), mmax(s->dt, 1), m, L))
+    return set_error(SV_EUNSUPPORTED, "a fused block does not fit a shared-memory tile");
+  std::vector<PassPlan> passes = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, kMaxMatPerPass);
+  if (passes.empty() && !out.blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
+  BuildCtx b{s->dt, s->n, m, L, 1, 0};
+  for (const PassPlan &P : passes) SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
+  out.lay = layout_of(out.prog, 0, 0);
+  return SV_OK;
+}
+
+static sv_status run_blocks_per_gate(sv_state *s, const std::vector<Block> &blocks) {
+  for (const Block &b : blocks) {
+    if (b.diag && b.qubits.size() + b.controls.size() <= 8) {
+      const int d = 1 << (int)b.qubits.size();
+      std::vector<cd> dg(d);
+      for (int r = 0; r < d; r++) dg[r] = b.U[(size_t)r * d + r];
+      SV_TRY(launch_diag_gate(s, b.qubits, b.controls, dg));
+    } else {
+      SV_TRY(launch_dense_gate(s, b.qubits, b.controls, b.U));
+    }
+  }
+  return SV_OK;
+}
+
+static sv_status upload_program(sv_state *s, const CachedProgram &cp, uint64_t key) {
+  if (s->resident_key == key && key != 0) return SV_OK;
+  const DeviceProgram &p = cp.prog;
+  std::vector<std::pair<const void *, size_t>> parts = {
+      {p.ops.data(), p.ops.size() * sizeof(TileOp)},
+      {p.mats.data(), p.mats.size()},
+      {p.coeffs.data(), p.coeffs.size() * sizeof(double)}};
+  std::vector<size_t> offs = {cp.lay.ops_off, cp.lay.mats_off, cp.lay.coeffs_off};
+  SV_TRY(stage_upload(s, parts, offs, cp.lay.end));
+  s->resident_key = key;
+  return SV_OK;
+}
+
+}  // namespace sv
+
+using namespace sv;
+static_assert(sizeof(sv_op) == 104, "sv_op layout is part of the ABI");
+static_assert(sizeof(sv_pauli_term) == 24, "sv_pauli_term layout is part of the ABI");
+static_assert(sizeof(sv_options) == 24, "sv_options layout is part of the ABI");
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *sv_last_error(void) { return g_err.c_str(); }
+
+const char *sv_status_string(sv_status st) {
+  switch (st) {
+    case SV_OK: return "SV_OK";
+    case SV_EINVAL: return "SV_EINVAL";
+    case SV_ENOMEM: return "SV_ENOMEM";
+    case SV_ECUDA: return "SV_ECUDA";
+    case SV_ETIMEOUT: return "SV_ETIMEOUT";
+    case SV_EUNSUPPORTED: return "SV_EUNSUPPORTED";
+    default: return "unknown";
+  }
+}
+
+uint64_t sv_kernel_launch_count(void) { return g_launches.load(); }
+
+size_t sv_workspace_bytes(int n, sv_dtype dt) {
+  (void)dt;
+  if (n < 1 || n > 34) return 0;
+  return kWsRed + red_bytes(n);
+}
+
+sv_status sv_create(int n, sv_dtype dt, void *amps, size_t amps_bytes, void *ws, size_t ws_bytes,
+                    void *stream, sv_state **out) {
+  if (!out) return set_error(SV_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 34) return set_error(SV_EINVAL, "n_qubits must be in [1, 34]");
+  if (dt != SV_C64 && dt != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+  if (!amps || !ws) return set_error(SV_EINVAL, "null device pointer");
+  if (((uintptr_t)amps & 255) || ((uintptr_t)ws & 255))
+    return set_error(SV_EINVAL, "device buffers must be 256-byte aligned");
+  if (amps_bytes < ((size_t)1 << n) * amp_bytes(dt)) return set_error(SV_EINVAL, "amplitude buffer too small");
+  if (ws_bytes < sv_workspace_bytes(n, dt))
+    return set_error(SV_ENOMEM, "workspace smaller than sv_workspace_bytes()");
+  cudaPointerAttributes attr;
+  SV_CUDA(cudaPointerGetAttributes(&attr, amps));
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return set_error(SV_EINVAL, "amplitudes must be device memory");
+  sv_state *s = new (std::nothrow) sv_state();
+  if (!s) return set_error(SV_ENOMEM, "host allocation failed");
+  s->n = n;
+  s->dt = dt;
+  s->amps = amps;
+  s->amps_bytes = amps_bytes;
+  s->ws = (char *)ws;
+  s->ws_bytes = ws_bytes;
+  s->stream = (cudaStream_t)stream;
+  s->device = attr.device;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != s->device) cudaSetDevice(s->device);
+  cudaError_t e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&s->pinned, kPinnedBytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->staged, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(s->staged, s->stream);
+  if (e != cudaSuccess) {
+    if (s->pinned) cudaFreeHost(s->pinned);
+    delete s;
+    return cuda_error(e, "sv_create");
+  }
+  s->pinned_bytes = kPinnedBytes;
+  *out = s;
+  return SV_OK;
+}
+
+sv_status sv_destroy(sv_state *s) {
+  if (!s) return SV_OK;
+  cudaStreamSynchronize(s->stream);
+  for (auto it = g_cache.begin(); it != g_cache.end();)
+    it = (it->first.first == s) ? g_cache.erase(it) : std::next(it);
+  if (s->staged) cudaEventDestroy(s->staged);
+  if (s->pinned) cudaFreeHost(s->pinned);
+  delete s;
+  return SV_OK;
+}
+
+sv_status sv_set_basis(sv_state *s, uint64_t index) {
+  if (!s) return set_error(SV_EINVAL, "null state");
+  if (index >= (1ull << s->n)) return set_error(SV_EINVAL, "basis index out of range");
+  return launch_set_basis(s, index);
+}
+
+sv_status sv_upload(sv_state *s, const void *host, size_t bytes) {
+  if (!s || !host) return set_error(SV_EINVAL, "null argument");
+  if (bytes != ((size_t)1 << s->n) * amp_bytes(s->dt)) return set_error(SV_EINVAL, "size mismatch");
+  SV_CUDA(cudaMemcpyAsync(s->amps, host, bytes, cudaMemcpyHostToDevice, s->stream));
+  SV_CUDA(cudaStreamSynchronize(s->stream));
+  return SV_OK;
+}
+
+sv_status sv_download(sv_state *s, void *host, size_t bytes) {
+  if (!s || !host) return set_error(SV_EINVAL, "null argument");
+  if (bytes != ((size_t)1 << s->n) * amp_bytes(s->dt)) return set_error(SV_EINVAL, "size mismatch");
+  SV_CUDA(cudaMemcpyAsync(host, s->amps, bytes, cudaMemcpyDeviceToHost, s->stream));
+  SV_CUDA(cudaStreamSynchronize(s->stream));
+  return SV_OK;
+}
+
+sv_status sv_synchronize(sv_state *s) {
+  if (!s) return set_error(SV_EINVAL, "null state");
+  SV_CUDA(cudaStreamSynchronize(s->stream));
+  return SV_OK;
+}
+
+sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_t *controls, int nctrl,
+                        const double *matrix, int adjoint) {
+  if (!s || !targets || !matrix) return set_error(SV_EINVAL, "null argument");
+  if (k < 1 || k > 6) return set_error(SV_EINVAL, "k must be in [1, 6]");
+  if (nctrl < 0 || nctrl > 8 || (nctrl > 0 && !controls)) return set_error(SV_EINVAL, "bad controls");
+  uint64_t seen = 0;
+  std::vector<int> t(k), c(nctrl);
+  for (int j = 0; j < k + nctrl; j++) {
+    const int q = j < k ? targets[j] : controls[j - k];
+    if (q < 0 || q >= s->n) return set_error(SV_EINVAL, "qubit out of range");
+    if ((seen >> q) & 1) return set_error(SV_EINVAL, "duplicate qubit (or control overlaps a target)");
+    seen |= 1ull << q;
+    (j < k ? t[j] : c[j - k]) = q;
+  }
+  const int d = 1 << k;
+  std::vector<cd> U((size_t)d * d);
+  for (int e = 0; e < d * d; e++) U[e] = cd(matrix[2 * e], matrix[2 * e + 1]);
+  if (adjoint) U = adjoint_of(U, k);
+  bool diag = true;
+  for (int r = 0; r < d && diag; r++)
+    for (int cc = 0; cc < d; cc++)
+      if (r != cc && U[(size_t)r * d + cc] != cd(0.0)) {
+        diag = false;
+        break;
+      }
+  if (diag && k + nctrl <= 8) {
+    std::vector<cd> dg(d);
+    for (int r = 0; r < d; r++) dg[r] = U[(size_t)r * d + r];
+    return launch_diag_gate(s, t, c, dg);
+  }
+  return launch_dense_gate(s, t, c, U);
+}
+
+sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt) {
+  if (!s) return set_error(SV_EINVAL, "null state");
+  if (!c) return set_error(SV_EINVAL, "null circuit");
+  const Opts o = resolve(s, opt, 1);
+  Hasher H;
+  H.val(circuit_hash(c, 0x51));
+  H.val(o.fusion_k);
+  H.val(o.tile_m);
+  H.val(o.L);
+  H.val(o.mode);
+  H.val((int)s->dt);
+  if (params && c->n_params > 0) H.bytes(params, sizeof(double) * c->n_params);
+  const uint64_t key = H.h;
+  auto ck = std::make_pair((const sv_state *)s, key);
+  auto it = g_cache.find(ck);
+  if (it == g_cache.end()) {
+    std::vector<Gate> gates;
+    SV_TRY(circuit_to_gates(c, params, s->n, gates, false));
+    CachedProgram cp;
+    SV_TRY(build_circuit_program(s, gates, o, cp));
+    if (g_cache.size() > 64) g_cache.clear();
+    it = g_cache.emplace(ck, std::move(cp)).first;
+  }
+  const CachedProgram &cp = it->second;
+  if (o.mode == SV_MODE_PER_GATE) return run_blocks_per_gate(s, cp.blocks);
+  SV_TRY(upload_program(s, cp, key));
+  LaunchEnv E;
+  E.v0 = s->amps;
+  return launch_program(s, cp.prog, cp.lay, cp.op0s, E);
+}
+
+}  // extern "C"

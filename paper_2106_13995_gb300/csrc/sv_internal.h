@@ -1,0 +1,249 @@
+// Internal declarations shared by the library's translation units.
+// Host-side structures (state handle, programs) and the device-side program
+// format read by the tile-pass kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <complex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/sv_api.h"
+
+namespace sv {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+sv_status set_error(sv_status st, const std::string &msg);
+sv_status cuda_error(cudaError_t e, const char *what);
+extern std::atomic<uint64_t> g_launches;
+
+#define SV_CUDA(call)                                            \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return ::sv::cuda_error(e_, #call);   \
+  } while (0)
+
+#define SV_TRY(call)                      \
+  do {                                    \
+    sv_status s_ = (call);                \
+    if (s_ != SV_OK) return s_;           \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device program format for tile passes
+// ---------------------------------------------------------------------------
+enum TileOpKind : uint8_t {
+  TOP_DENSE = 0,     // v <- U v on local targets (k = 1..6), local + global controls
+  TOP_DIAG = 1,      // v[l] <- d[r(l)] v[l], r over local targets
+  TOP_GRAD = 2,      // acc[slot] += Im <v1 | G v0>, G = X/Y/Z/P1(-2) on one local target
+  TOP_PAULI = 3,     // v1[l ^ xm] += c * phase * (-1)^{popcount(l & zm)} v0[l]
+  TOP_ZERO = 4,      // v1 <- 0
+  TOP_DOT = 5        // acc[slot] += Re <v0 | v1>
+};
+
+// 32-byte op descriptor; matrices live in a separate pool.
+struct TileOp {
+  uint8_t kind;
+  uint8_t k;          // number of targets
+  uint8_t vmask;      // bit0: apply to v0, bit1: apply to v1
+  uint8_t gen;        // TOP_GRAD generator: 1=X 2=Y 3=Z 4=diag(0,-2)
+  uint8_t t[6];       // local target positions, matrix bit order
+  uint8_t ts[6];      // the same positions sorted ascending
+  uint32_t lcmask;    // local control mask (bits of the tile-local index)
+  uint32_t mat;       // offset (complex entries) into the matrix pool; TOP_PAULI: coeff index
+  uint32_t gcmask_lo; // controls outside the tile, as a mask of global bits (low 32)
+  uint16_t gcmask_hi; // ... bits 32..47
+  int16_t slot;       // accumulator slot (TOP_GRAD / TOP_DOT); TOP_PAULI: x mask (local)
+};
+static_assert(sizeof(TileOp) == 32, "TileOp must stay 32 bytes");
+
+// Per-pass launch description (passed by value as a kernel parameter).
+constexpr int kMaxQ = 34;
+constexpr uint8_t kGenBatchMat = 0x80;   // TileOp.gen flag: matrix from the per-batch pool
+struct TilePass {
+  int32_t n;              // state qubits
+  int32_t m;              // tile qubits
+  int32_t L;              // low qubits included in every tile (contiguous segment 2^L)
+  int32_t nops;
+  int8_t hi_pos[kMaxQ];   // global position of local bit L + j
+  int8_t out_pos[kMaxQ];  // sorted global positions not in the tile (n - m of them)
+  uint32_t flags;         // bit0: v1 is zeroed by the pass, do not load it
+  uint32_t nvec;          // 1 or 2 vectors per tile
+  const TileOp *ops;      // device: this pass's ops
+  const void *mats;       // device: shared matrix pool
+  const void *pmats;      // device: per-batch matrix pool
+  uint64_t pmats_stride;  // complex entries per batch item
+  const double *coeffs;   // device: TOP_PAULI coefficients
+  double *acc;            // device: FP64 accumulators
+  uint64_t acc_stride;    // doubles per batch item
+  void *const *tbl0;      // device: per-batch pointers of vector 0 (or null)
+  void *const *tbl1;      // device: per-batch pointers of vector 1 (or null)
+  void *v0;               // vector 0 when tbl0 is null
+  void *v1;               // vector 1 when tbl1 is null
+};
+
+// ---------------------------------------------------------------------------
+// host-side gate representation and planners
+// ---------------------------------------------------------------------------
+struct Gate {
+  std::vector<int> targets;    // matrix bit j <-> targets[j]
+  std::vector<int> controls;
+  std::vector<cd> U;           // 2^k x 2^k row-major
+  int param_gate = -1;         // sv_gate for parametric gates (adjoint generator)
+  int param = -1;              // parameter index or -1
+  bool fixed_structure = false;  // never fuse (parametric in batched programs)
+  int inst = -1;               // parametric instance index (per-batch matrix table)
+  int grad_gen = 0;            // >0: gradient probe Im<v1|G v0> instead of a gate
+  int grad_slot = -1;
+};
+
+struct Block {
+  std::vector<int> qubits;     // targets (matrix bit order)
+  std::vector<int> controls;   // remaining controls (unfused controlled gates)
+  std::vector<cd> U;
+  bool diag = false;
+  bool fusable = true;
+  int param = -1;              // parametric single gate (batched / gradient)
+  int param_gate = -1;
+  int kind = TOP_DENSE;        // TOP_DENSE / TOP_GRAD / ...
+  int gen = 0;
+  int vmask = 1;
+  int slot = -1;
+  int inst = -1;               // parametric instance (per-batch matrix)
+  double coeff = 0;
+  uint64_t xmask = 0, zmask = 0;
+};
+
+// gates.cpp
+int gate_arity(int gate);                                    // -1 unknown
+bool gate_matrix(int gate, const double *angles, std::vector<cd> &U);
+int gate_generator(int gate);                                // 1=X 2=Y 3=Z 4=diag(0,-2), 0 none
+sv_status circuit_to_gates(const sv_circuit *c, const double *params, int n,
+                           std::vector<Gate> &out, bool keep_params_unfused);
+std::vector<cd> adjoint_of(const std::vector<cd> &U, int k);
+
+// planner.cpp
+std::vector<Block> fuse(const std::vector<Gate> &gates, int fusion_k);
+struct PassPlan {
+  std::vector<int> S;          // tile qubits: S[0..L) = 0..L-1, then sorted high qubits
+  std::vector<Block> ops;
+};
+int max_targets(const std::vector<Block> &blocks);
+// Shrink L (keeping >= lmin) or grow m (up to mmax, at most n) so that every
+// block's targets fit one tile.  False if impossible.
+bool fit_tile(const std::vector<Block> &blocks, int n, int lmin, int mmax, int &m, int &L);
+// Empty result when some block cannot fit a tile of m qubits with L fixed low
+// qubits (callers size m and L with fit_tile first).
+std::vector<PassPlan> plan_passes(const std::vector<Block> &blocks, int n, int m, int L,
+                                  int max_ops, int max_mat_entries);
+
+// ---------------------------------------------------------------------------
+// state handle
+// ---------------------------------------------------------------------------
+struct DeviceProgram {
+  std::vector<TilePass> passes;
+  std::vector<TileOp> ops;
+  std::vector<uint8_t> mats;      // matrix pool bytes (dtype of the state)
+  std::vector<double> coeffs;     // TOP_PAULI coefficients
+  uint32_t n_slots = 0;
+};
+
+}  // namespace sv
+
+struct sv_state {
+  int n = 0;
+  sv_dtype dt = SV_C64;
+  void *amps = nullptr;
+  size_t amps_bytes = 0;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  // pinned host staging
+  char *pinned = nullptr;
+  size_t pinned_bytes = 0;
+  cudaEvent_t staged = nullptr;     // last upload from `pinned` finished
+  // program cache: key -> program
+  std::unordered_map<uint64_t, sv::DeviceProgram> programs;
+  uint64_t resident_key = 0;        // program currently in the workspace program area
+};
+
+namespace sv {
+
+// workspace layout (byte offsets)
+constexpr size_t kWsCtrl = 0;                    // flags, counters, scalars
+constexpr size_t kWsCtrlBytes = 256 << 10;
+constexpr size_t kWsProg = kWsCtrlBytes;         // uploaded programs
+constexpr size_t kWsProgBytes = 8 << 20;
+constexpr size_t kWsRed = kWsProg + kWsProgBytes;  // reduction / sampling area
+size_t red_bytes(int n);
+constexpr size_t kPinnedBytes = kWsProgBytes + kWsCtrlBytes;
+
+size_t amp_bytes(sv_dtype dt);
+int lmin(sv_dtype dt);            // low qubits a tile must keep contiguous (16-byte copies)
+int mmax(sv_dtype dt, int nvec);  // largest tile that fits shared memory
+constexpr size_t kWsScalars = 0;            // FP64 result slots (4 KB)
+constexpr size_t kWsGateMat = 64 << 10;     // single-gate matrix scratch (k >= 4)
+
+// program building / upload / launch (sv_api.cu)
+struct BuildCtx {
+  sv_dtype dt;
+  int n, m, L;
+  uint32_t nvec;
+  uint32_t flags;
+};
+sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
+                    std::vector<uint32_t> &op0s, const std::vector<int> &batch_mat_off);
+struct ProgLayout {
+  size_t ops_off, mats_off, coeffs_off, tbl_off, pmats_off, end;
+};
+ProgLayout layout_of(const DeviceProgram &p, size_t tbl_bytes, size_t pmats_bytes);
+sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, size_t>> &parts,
+                       const std::vector<size_t> &offs, size_t total);
+struct LaunchEnv {
+  int batch = 1;
+  void *const *tbl0 = nullptr;
+  void *const *tbl1 = nullptr;
+  void *v0 = nullptr, *v1 = nullptr;
+  const void *pmats = nullptr;
+  uint64_t pmats_stride = 0;
+  double *acc = nullptr;
+  uint64_t acc_stride = 0;
+};
+sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &L,
+                         const std::vector<uint32_t> &op0s, const LaunchEnv &E);
+struct Opts {
+  int fusion_k, tile_m, L, prec, mode;
+};
+Opts resolve(const sv_state *s, const sv_options *o, int nvec);
+uint64_t circuit_hash(const sv_circuit *c, uint64_t salt);
+
+// kernels (launchers), all enqueue on s->stream
+sv_status launch_set_basis(sv_state *s, uint64_t index);
+sv_status launch_scale(sv_state *s, double factor);
+sv_status launch_dense_gate(sv_state *s, const std::vector<int> &targets,
+                            const std::vector<int> &controls, const std::vector<cd> &U);
+sv_status launch_diag_gate(sv_state *s, const std::vector<int> &targets,
+                           const std::vector<int> &controls, const std::vector<cd> &d);
+sv_status launch_norm(sv_state *s, double *out_dev_scalar);
+sv_status launch_expect_group(sv_state *s, uint64_t xmask, const uint64_t *zm, const double *cf,
+                              const int *ipow, int nt, double *out_dev);
+sv_status launch_z_all(sv_state *s, double *out_dev);
+sv_status launch_sample_prepare(sv_state *s);
+sv_status launch_sample_shots(sv_state *s, int64_t shot0, int64_t count, uint64_t seed, uint64_t *out_dev);
+size_t sample_shot_offset(int n);
+int64_t sample_shot_capacity();
+sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch);
+int tile_threads(int m, sv_dtype dt);
+size_t tile_smem(sv_dtype dt, int m, int nvec);
+
+}  // namespace sv

@@ -1,0 +1,159 @@
+"""GPU parity of whole circuits (fusion planner + tile passes) against the
+FP64 oracle: the 12-qubit random U3+CZ case, mixed random circuits under
+every fusion width and tile size, grid circuits, closed forms and the
+quantum multiplier."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import fidelity_metrics
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(svlib, circ, dt, psi0=None, opts=None, params=None):
+    s = svlib.StateVector(circ.n_qubits, dt)
+    if psi0 is None:
+        s.set_basis(0)
+    else:
+        s.load(psi0)
+    s.apply_circuit(circ, params=params, opts=opts)
+    return s
+
+
+def test_random_u3cz_12q_c128(svlib, oracle):
+    """12 qubits, 20 layers, complex128: 1-F <= 1e-12, <Z_i> within 1e-12."""
+    c = W.random_u3_cz(12, 20, 0)
+    want = oracle.run(c)
+    for opts in (None, svlib.options(mode=1), svlib.options(fusion_k=1), svlib.options(fusion_k=5, tile_m=9)):
+        s = run_gpu(svlib, c, "c128", opts=opts)
+        inf, amp = fidelity_metrics(want, s.numpy())
+        assert inf <= 1e-12 and amp <= 1e-13, (opts, inf, amp)
+        z = s.z_all()
+        assert np.max(np.abs(z - oracle.z_all(want))) <= 1e-12
+        assert abs(s.norm2() - 1) <= 1e-13
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("fk", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("m", [6, 10, 13])
+def test_mixed_random_all_fusions_and_tiles(svlib, oracle, dt, fk, m):
+    n = 14
+    c = W.random_gate_circuit(n, 120, seed=fk * 100 + m)
+    psi0 = W.random_state(n, np.random.default_rng(m))
+    cast = psi0.astype(np.complex64 if dt == "c64" else np.complex128).astype(np.complex128)
+    want = oracle.run(c, cast)
+    s = run_gpu(svlib, c, dt, psi0=psi0, opts=svlib.options(fusion_k=fk, tile_m=m))
+    inf, amp = fidelity_metrics(want, s.numpy())
+    tol = 1e-5 if dt == "c64" else 1e-12
+    assert inf <= tol, (inf, amp)
+
+
+@pytest.mark.parametrize("n", [3, 5, 9])
+def test_small_states_single_tile(svlib, oracle, n):
+    c = W.random_gate_circuit(n, 40, seed=n, kmax=min(3, n))
+    want = oracle.run(c)
+    for dt, tol in (("c64", 1e-5), ("c128", 1e-12)):
+        inf, _ = fidelity_metrics(want, run_gpu(svlib, c, dt).numpy())
+        assert inf <= tol
+
+
+def test_grid_4x4(svlib, oracle):
+    c = W.grid_random(4, 4, 8, seed=1)
+    want = oracle.run(c)
+    for opts in (None, svlib.options(mode=1), svlib.options(fusion_k=4, tile_m=11)):
+        inf, amp = fidelity_metrics(want, run_gpu(svlib, c, "c64", opts=opts).numpy())
+        assert inf <= 1e-5, (opts, inf)
+
+
+def test_grid_26q_instance(svlib, oracle):
+    """The 26-qubit width-reduced 5x6 grid circuit, complex64 vs FP64 oracle."""
+    c = W.remove_qubits(W.grid_random(5, 6, 20, seed=1), 4, seed=101)
+    want = oracle.run(c)
+    s = run_gpu(svlib, c, "c64")
+    got = s.numpy()
+    inf, amp = fidelity_metrics(want, got)
+    assert inf <= 1e-5, inf
+    print(f"grid 26q c64: 1-F = {inf:.3e}, max |d psi| = {amp:.3e}")
+
+
+def test_ghz_and_qft(svlib, oracle):
+    for dt in ("c64", "c128"):
+        n = 20
+        v = run_gpu(svlib, W.ghz(n), dt).numpy()
+        r = np.float32(1 / math.sqrt(2)) if dt == "c64" else 1 / math.sqrt(2)
+        assert v[0] == r and v[-1] == r and np.count_nonzero(v) == 2
+        n = 10
+        x = 337
+        q = run_gpu(svlib, W.concat(W.basis_prep(n, x), W.qft(n)), dt).numpy()
+        want = np.exp(2j * math.pi * x * np.arange(1 << n) / (1 << n)) / math.sqrt(1 << n)
+        tol = 1e-6 if dt == "c64" else 1e-13
+        assert np.max(np.abs(q - want)) <= tol
+
+
+def test_multiplier_3bit_all_inputs(svlib):
+    nb = 3
+    c = W.multiplier(nb)
+    for a in range(8):
+        for b in range(8):
+            s = svlib.StateVector(c.n_qubits, "c64").set_basis(W.multiplier_basis_index(a, b, nb))
+            s.apply_circuit(c)
+            v = s.numpy()
+            idx = W.multiplier_basis_index(a, b, nb, a * b)
+            assert v[idx] == 1 and np.count_nonzero(v) == 1
+
+
+def test_multiplier_29q_basis_inputs(svlib):
+    """Full width: 7-bit x 7-bit multiplier, 64 seeded basis inputs; the
+    output bits are read from <Z_q> = 1 - 2 bit_q (exactly +-1)."""
+    nb = 7
+    c = W.multiplier(nb)
+    m = svlib.marshal(c)
+    rng = np.random.default_rng(2)
+    s = svlib.StateVector(c.n_qubits, "c64")
+    for a, b in rng.integers(0, 128, size=(64, 2)):
+        a, b = int(a), int(b)
+        s.set_basis(W.multiplier_basis_index(a, b, nb))
+        s.apply_circuit(m)
+        z = s.z_all()
+        bits = (z < 0).astype(np.int64)
+        idx = int(sum(int(v) << q for q, v in enumerate(bits)))
+        assert idx == W.multiplier_basis_index(a, b, nb, a * b)
+        assert np.all(np.abs(np.abs(z) - 1) <= 1e-6)
+
+
+def test_multiplier_superposed_inputs(svlib):
+    """H on both inputs: probability 2^-2nb on every |a,b,ab,0> (within
+    1e-6 relative: 1/sqrt(2) is rounded in FP32) and exactly 0 elsewhere
+    (the multiplier only permutes amplitudes)."""
+    nb = 5
+    c = W.multiplier(nb, hadamard_inputs=True)
+    v = run_gpu(svlib, c, "c64").numpy()
+    p = np.abs(v.astype(np.complex128)) ** 2
+    want = np.zeros_like(p)
+    for a in range(1 << nb):
+        for b in range(1 << nb):
+            want[W.multiplier_basis_index(a, b, nb, a * b)] = 2.0 ** (-2 * nb)
+    assert np.array_equal(p != 0, want != 0)
+    assert np.max(np.abs(p - want)) <= 1e-6 * 2.0 ** (-2 * nb)
+    # full width, checked by sampling: every shot decodes to (a, b, a*b, 0)
+    nb = 7
+    s = run_gpu(svlib, W.multiplier(nb, hadamard_inputs=True), "c64")
+    shots = s.sample(4096, 99)
+    for x in shots.tolist():
+        a, b = x & 127, (x >> 7) & 127
+        assert x == W.multiplier_basis_index(a, b, nb, a * b)
+    assert abs(s.norm2() - 1) <= 1e-6
+
+
+def test_program_cache_reuse_and_params(svlib, oracle):
+    c = W.hea(8, 2)
+    p1 = W.hea_params(2, c.n_params, 5)
+    m = svlib.marshal(c)
+    s = svlib.StateVector(8, "c128")
+    for p in p1:
+        s.set_basis(0).apply_circuit(m, params=p)
+        inf, _ = fidelity_metrics(oracle.run(c, params=p), s.numpy())
+        assert inf <= 1e-12
