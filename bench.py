@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 state-vector simulator.
+
+Workload (one "step"): the 30-qubit 5x6 grid random circuit (20 cycles of
+random sqrt(X)/sqrt(Y)/sqrt(W) layers and fSim(pi/2, pi/6) couplers in the
+ABCDCDAB pattern, 845 gates) on a complex64 state of 2^30 amplitudes (8 GiB),
+covering every step of the hot path: |0...0> initialisation, the fused and
+tiled gate passes, <Z_q> for all qubits, a diagonal Pauli energy, the norm
+and 1000 measurement samples.  value = gates/s over the whole job.
+
+Also reported: e2e (the same step through the C ABI starting from a pinned
+host state, host<->device copies inside the timed region), the roofline of the
+dominant kernel (the tile pass), single-gate passes at 30 qubits per target,
+adjoint gradients of the 20-qubit ansatz batched (64 parameter sets per
+launch sequence) vs plain (one call per set), and the FP64 CPU oracle timed on
+this host's cores.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "gates/s + HBM GB/s at 30q vs roofline; adjoint grads/s batched vs plain"
+UNIT = "gates/s"
+TILE_KERNEL_SRC = os.path.join(ROOT, "paper_2106_13995_gb300", "csrc", "k_tile.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tile_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--qubits", type=int, default=30,
+                    help="30 = the 5x6 grid; fewer = the same grid with random qubits removed")
+    ap.add_argument("--sections", default="all",
+                    help="comma list of step,e2e,roofline,single,adjoint,cpu (default all)")
+    return ap.parse_args()
+
+
+def workload(nq: int):
+    c = W.grid_random(5, 6, 20, seed=1)
+    if nq < 30:
+        c = W.remove_qubits(c, 30 - nq, seed=101)
+    return c
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on host cores (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(circ, budget_s: float, max_gates=None):
+    """Apply the circuit's gates one by one with the FP64 oracle to a 2^n
+    complex128 state until the time budget is spent.  Returns (gates/s,
+    gates done, seconds, threads, n)."""
+    import oracle
+    oracle.build()
+    n = circ.n_qubits
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1
+    done, t0 = 0, time.perf_counter()
+    for op in circ.ops:
+        oracle.run_inplace(W.Circuit(n, [op]), psi)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_gates and done >= max_gates):
+            break
+    el = time.perf_counter() - t0
+    return done / el, done, el, oracle.num_threads(), n
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    circ = workload(args.qubits)
+    # warm-up then timed steps; each step applies the first 4 gates of the
+    # circuit with the FP64 oracle to a fresh 2^n complex128 state
+    per_step = 4
+    times = []
+    for i in range(args.warmup + args.steps):
+        gs, done, el, thr, n = oracle_sample(circ, 1e9, max_gates=per_step)
+        if i >= args.warmup:
+            times.append(el)
+    total = sum(times)
+    value = per_step * len(times) / total
+    sample = f"first {per_step} gates of the {circ.n_qubits}-qubit grid circuit per step, FP64 oracle, complex128 state"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_of(circ, args),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_of(circ, args):
+    return {"workload": f"grid random circuit 5x6 lattice (30 qubits{'' if circ.n_qubits == 30 else f', {30 - circ.n_qubits} removed'}),"
+                        f" 20 cycles, {len(circ.ops)} gates, complex64 state",
+            "n_qubits": circ.n_qubits, "gates": len(circ.ops), "state_dtype": "complex64",
+            "state_bytes": (1 << circ.n_qubits) * 8,
+            "l2": "inputs larger than L2: the state is 8 GiB (L2 129 MB)" if circ.n_qubits >= 25 else "small state",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    import paper_2106_13995_gb300 as P
+    if rank == 0:
+        P.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2106_13995_gb300 import sim
+
+    sections = set(args.sections.split(",")) if args.sections != "all" else \
+        {"step", "e2e", "roofline", "single", "adjoint", "cpu"}
+    circ = workload(args.qubits)
+    n = circ.n_qubits
+    m = sim.marshal(circ)
+    stream = torch.cuda.current_stream(dev)
+    state = sim.StateVector(n, "c64", device=dev)
+    zz = [(0, (1 << a) | (1 << b), 1.0) for pat in W.grid_couplers(5, 6).values() for a, b in pat
+          if a < n and b < n]
+    shots = np.zeros(1000, dtype=np.uint64)
+
+    def step():
+        state.set_basis(0)
+        state.apply_circuit(m)
+        z = state.z_all()
+        e = state.expect(zz)
+        nrm = state.norm2()
+        s = state.sample(1000, 7)
+        return z, e, nrm, s
+
+    def timed(fn, k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t
+
+    out = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": config_of(circ, args)}
+    nblocks, npasses = state.plan_info(m)
+    out["config"]["fused_blocks"] = nblocks
+    out["config"]["tile_passes"] = npasses
+
+    # ---- main timed region ----------------------------------------------------
+    for _ in range(args.warmup):
+        step()
+    l0 = sim.kernel_launches()
+    with ClockSampler(local) as clk:
+        t = timed(step, args.steps)
+    launches = sim.kernel_launches() - l0
+    out["value"] = len(circ.ops) * args.steps * world / t
+    out["ms_per_step"] = 1e3 * t / args.steps
+    out["gpu_launches"] = int(launches)
+    out["clocks"] = clk.summary()
+    gate_bytes = 2 * (1 << n) * 8
+    out["hbm_gbs_effective"] = len(circ.ops) * gate_bytes * args.steps / t / 1e9
+
+    # ---- roofline of the dominant kernel (the tile pass) -----------------------
+    peak, peak_src = measured_peaks()
+    if "roofline" in sections:
+        reps = max(2, args.steps // 2)
+        state.set_basis(0)
+        tc = timed(lambda: state.apply_circuit(m), reps) / reps
+        per_launch = tc / npasses
+        achieved = gate_bytes / per_launch / 1e9
+        traffic = None
+        try:
+            with open(TRAFFIC_FILE) as f:
+                tr = json.load(f)
+            src_hash = hashlib.sha256(open(TILE_KERNEL_SRC, "rb").read()).hexdigest()[:16]
+            if tr.get("k_tile_sha") == src_hash and tr.get("n_qubits") == n:
+                traffic = tr["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+        out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "traffic": traffic, "kernel": "k_tile<float> (tile pass)",
+                           "algorithmic_bytes_per_launch": gate_bytes, "launches_per_circuit": npasses,
+                           "avg_launch_ms": per_launch * 1e3, "peak_source": peak_src}
+
+    # ---- single-gate passes per target (K1-K3) ---------------------------------
+    if "single" in sections:
+        U = W.random_unitary(1, np.random.default_rng(0))
+        gbs = {}
+        for q in sorted(set([0, 1, 3, 5, 6, 12, 20, n - 1])):
+            tq = timed(lambda: state.apply_gate(U, [q]), 5) / 5
+            gbs[q] = gate_bytes / tq / 1e9
+        vals = list(gbs.values())
+        out["single_gate_pass"] = {"gbs_by_target": {str(k): round(v, 1) for k, v in gbs.items()},
+                                   "min_gbs": min(vals), "mean_gbs": statistics.mean(vals),
+                                   "min_frac_of_measured": min(vals) / peak,
+                                   "gates_per_s_min": min(vals) * 1e9 / gate_bytes}
+
+    # ---- end to end through the C ABI from host buffers -----------------------
+    if "e2e" in sections:
+        host = torch.zeros(2 << n, dtype=torch.float32, pin_memory=True)
+        host[0] = 1.0
+        hp = host.data_ptr()
+
+        def step_e2e():
+            from paper_2106_13995_gb300 import _native as N
+            N.check(N.lib().sv_upload(state.h, hp, state.nbytes))
+            state.apply_circuit(m)
+            z = state.z_all()
+            e = state.expect(zz)
+            s = state.sample(1000, 7)
+            return z, e, s
+
+        for _ in range(max(1, args.warmup)):
+            step_e2e()
+        ke = max(2, args.steps // 2)
+        te = timed(step_e2e, ke)
+        out["e2e"] = {"value": len(circ.ops) * ke * world / te, "unit": UNIT,
+                      "h2d_bytes_per_step": state.nbytes, "d2h_bytes_per_step": 8 * n + 8 + 8 * 1000,
+                      "ms_per_step": 1e3 * te / ke}
+        del host
+
+    # ---- adjoint gradients, batched vs plain (20-qubit ansatz, 64 sets) ----------
+    if "adjoint" in sections:
+        del state
+        torch.cuda.empty_cache()
+        na, B = 20, 64
+        h = W.hea(na, 10)
+        hm = sim.marshal(h)
+        terms = W.tfim(na)
+        params = W.hea_params(B, h.n_params, 3)
+        psis = [sim.StateVector(na, "c64", device=dev).set_basis(0) for _ in range(B)]
+        lams = [sim.StateVector(na, "c64", device=dev) for _ in range(B)]
+
+        def batched():
+            for p in psis:
+                p.set_basis(0)
+            return sim.adjoint_grad_batch(psis, lams, hm, params, terms)
+
+        def plain():
+            for b in range(B):
+                psis[b].set_basis(0)
+                sim.adjoint_grad(psis[b], lams[b], hm, params[b], terms)
+
+        for _ in range(max(1, args.warmup)):
+            batched()
+        plain()
+        kb = max(2, args.steps // 2)
+        tb = timed(batched, kb) / kb
+        tp = timed(plain, 1)
+        out["adjoint"] = {"grads_per_s_batched": B / tb, "grads_per_s_plain": B / tp,
+                          "speedup": tp / tb, "batch": B, "n_qubits": na, "gates": len(h.ops),
+                          "params": h.n_params, "state": "complex64, FP64 reductions"}
+        del psis, lams
+
+    # ---- the FP64 oracle on this host's cores ------------------------------------
+    if "cpu" in sections and rank == 0:
+        try:
+            gs, done, el, thr, nn = oracle_sample(circ, 15.0)
+            out["cpu_baseline"] = {"value": gs, "unit": UNIT, "cores": thr, "kind": "oracle",
+                                   "sample": f"first {done} of {len(circ.ops)} gates of the same {nn}-qubit circuit "
+                                             f"on a complex128 state, {el:.1f} s"}
+        except MemoryError:
+            out["cpu_baseline"] = None
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -176,6 +176,13 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
 sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params,
                            const sv_options *opt);
 
+/* Report how sv_apply_circuit would execute this circuit with these options:
+ * the number of fused blocks and of tile passes (one kernel launch, one read
+ * and one write of the state each).  Builds and caches the plan; launches
+ * nothing.  Same errors as sv_apply_circuit. */
+sv_status sv_plan_info(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
+                       int64_t *n_blocks, int64_t *n_passes);
+
 /* Apply the same circuit structure to B states (each with its own parameter
  * vector params[b], host FP64, may be NULL) in one launch sequence.  States
  * may have different widths only if circuits differ (circs[b] matches

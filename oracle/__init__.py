@@ -195,6 +195,17 @@ def run(circ, psi: Optional[np.ndarray] = None, params: Optional[np.ndarray] = N
     return psi
 
 
+def run_inplace(circ, psi: np.ndarray, params: Optional[np.ndarray] = None) -> np.ndarray:
+    """Same as run() but updates the caller's complex128 array in place."""
+    if psi.dtype != np.complex128 or not psi.flags.c_contiguous or psi.size != (1 << circ.n_qubits):
+        raise ValueError("psi must be a contiguous complex128 array of 2^n entries")
+    ops, keep = _marshal(circ)
+    p = np.ascontiguousarray(params if params is not None else np.zeros(1), dtype=np.float64)
+    if lib().or_run(_dp(psi.view(np.float64)), circ.n_qubits, ops, len(circ.ops), _dp(p)) != 0:
+        raise ValueError("malformed circuit")
+    return psi
+
+
 # --- observables ---------------------------------------------------------------
 
 def _terms(terms: Iterable[Tuple[int, int, float]]):

@@ -80,6 +80,8 @@ def lib():
             "sv_synchronize": (st, [vp]),
             "sv_apply_gate": (st, [vp, i32p, C.c_int, i32p, C.c_int, dp, C.c_int]),
             "sv_apply_circuit": (st, [vp, C.POINTER(SvCircuit), dp, C.POINTER(SvOptions)]),
+            "sv_plan_info": (st, [vp, C.POINTER(SvCircuit), dp, C.POINTER(SvOptions), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64)]),
             "sv_apply_circuit_batch": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.POINTER(SvCircuit)),
                                             C.POINTER(dp), C.POINTER(SvOptions)]),
             "sv_expect": (st, [vp, C.POINTER(SvPauliTerm), C.c_int, dp]),

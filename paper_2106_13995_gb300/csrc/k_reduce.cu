@@ -141,16 +141,18 @@ sv_status launch_norm(sv_state *s, double *out_dev) {
 // For one x_mask: sum_x Re( conj(psi[x ^ xm]) * F(x) * psi[x] ),
 // F(x) = sum_t c_t i^{k_t} (-1)^{popcount(x & zm_t)}.
 constexpr int kMaxGroupTerms = 64;
-struct ExpectArgs {
+// Coefficients are stored in the state's precision: converting FP64 to FP32
+// per amplitude would run on the (slow) FP64 pipe.
+template <typename R> struct ExpectArgs {
   uint64_t xm;
   int nt;
   uint64_t zm[kMaxGroupTerms];
-  double fr[kMaxGroupTerms], fi[kMaxGroupTerms];
+  R fr[kMaxGroupTerms], fi[kMaxGroupTerms];
 };
 
 template <typename R>
 __global__ void k_expect(const typename Cx<R>::T *__restrict__ a, uint64_t namps,
-                         const __grid_constant__ ExpectArgs A, double *partial) {
+                         const __grid_constant__ ExpectArgs<R> A, double *partial) {
   using C = typename Cx<R>::T;
   constexpr int RUN = 16;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -164,9 +166,9 @@ __global__ void k_expect(const typename Cx<R>::T *__restrict__ a, uint64_t namps
       const C v = a[x], w = a[x ^ A.xm];
       R fr = 0, fi = 0;
       for (int t = 0; t < A.nt; t++) {
-        const R sg = (__popcll(x & A.zm[t]) & 1) ? R(-1) : R(1);
-        fr += sg * (R)A.fr[t];
-        fi += sg * (R)A.fi[t];
+        const bool neg = __popcll(x & A.zm[t]) & 1;
+        fr += neg ? -A.fr[t] : A.fr[t];
+        fi += neg ? -A.fi[t] : A.fi[t];
       }
       // Re(conj(w) * (f * v))
       const R pr = fr * v.x - fi * v.y, pi = fr * v.y + fi * v.x;
@@ -177,32 +179,37 @@ __global__ void k_expect(const typename Cx<R>::T *__restrict__ a, uint64_t namps
   block_sum_to(acc, partial + blockIdx.x);
 }
 
-sv_status launch_expect_group(sv_state *s, uint64_t xm, const uint64_t *zm, const double *cf,
-                              const int *ipow, int nt, double *out_dev) {
-  if (nt > kMaxGroupTerms) return set_error(SV_EINVAL, "too many terms in one group");
-  ExpectArgs A{};
+template <typename R>
+static sv_status expect_launch(sv_state *s, uint64_t xm, const uint64_t *zm, const double *cf, const int *ipow,
+                               int nt, double *out_dev) {
+  ExpectArgs<R> A{};
   A.xm = xm;
   A.nt = nt;
   for (int t = 0; t < nt; t++) {
     A.zm[t] = zm[t];
     switch (ipow[t] & 3) {
-      case 0: A.fr[t] = cf[t]; break;
-      case 1: A.fi[t] = cf[t]; break;
-      case 2: A.fr[t] = -cf[t]; break;
-      default: A.fi[t] = -cf[t]; break;
+      case 0: A.fr[t] = (R)cf[t]; break;
+      case 1: A.fi[t] = (R)cf[t]; break;
+      case 2: A.fr[t] = (R)-cf[t]; break;
+      default: A.fi[t] = (R)-cf[t]; break;
     }
   }
   const uint64_t na = 1ull << s->n;
   double *partial = reinterpret_cast<double *>(s->ws + kWsRed);
   const int g = red_grid(s, na / 16 + 1);
-  if (s->dt == SV_C64)
-    k_expect<float><<<g, kRedThreads, 0, s->stream>>>((const float2 *)s->amps, na, A, partial);
-  else
-    k_expect<double><<<g, kRedThreads, 0, s->stream>>>((const double2 *)s->amps, na, A, partial);
+  k_expect<R><<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const typename Cx<R>::T *>(s->amps), na, A,
+                                                partial);
   k_finalize<<<1, 32, 0, s->stream>>>(partial, g, 1, out_dev);
   g_launches += 2;
   SV_CUDA(cudaGetLastError());
   return SV_OK;
+}
+
+sv_status launch_expect_group(sv_state *s, uint64_t xm, const uint64_t *zm, const double *cf,
+                              const int *ipow, int nt, double *out_dev) {
+  if (nt > kMaxGroupTerms) return set_error(SV_EINVAL, "too many terms in one group");
+  return s->dt == SV_C64 ? expect_launch<float>(s, xm, zm, cf, ipow, nt, out_dev)
+                         : expect_launch<double>(s, xm, zm, cf, ipow, nt, out_dev);
 }
 
 // ---- <Z_q> for every qubit in one pass -----------------------------------

@@ -426,7 +426,8 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
   return launch_dense_gate(s, t, c, U);
 }
 
-sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt) {
+static sv_status get_program(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
+                             const CachedProgram **out, uint64_t *key_out, Opts *o_out) {
   if (!s) return set_error(SV_EINVAL, "null state");
   if (!c) return set_error(SV_EINVAL, "null circuit");
   const Opts o = resolve(s, opt, 1);
@@ -449,12 +450,33 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *param
     if (g_cache.size() > 64) g_cache.clear();
     it = g_cache.emplace(ck, std::move(cp)).first;
   }
-  const CachedProgram &cp = it->second;
-  if (o.mode == SV_MODE_PER_GATE) return run_blocks_per_gate(s, cp.blocks);
-  SV_TRY(upload_program(s, cp, key));
+  *out = &it->second;
+  *key_out = key;
+  *o_out = o;
+  return SV_OK;
+}
+
+sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt) {
+  const CachedProgram *cp = nullptr;
+  uint64_t key = 0;
+  Opts o;
+  SV_TRY(get_program(s, c, params, opt, &cp, &key, &o));
+  if (o.mode == SV_MODE_PER_GATE) return run_blocks_per_gate(s, cp->blocks);
+  SV_TRY(upload_program(s, *cp, key));
   LaunchEnv E;
   E.v0 = s->amps;
-  return launch_program(s, cp.prog, cp.lay, cp.op0s, E);
+  return launch_program(s, cp->prog, cp->lay, cp->op0s, E);
+}
+
+sv_status sv_plan_info(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
+                       int64_t *n_blocks, int64_t *n_passes) {
+  const CachedProgram *cp = nullptr;
+  uint64_t key = 0;
+  Opts o;
+  SV_TRY(get_program(s, c, params, opt, &cp, &key, &o));
+  if (n_blocks) *n_blocks = (int64_t)cp->blocks.size();
+  if (n_passes) *n_passes = o.mode == SV_MODE_PER_GATE ? (int64_t)cp->blocks.size() : (int64_t)cp->prog.passes.size();
+  return SV_OK;
 }
 
 }  // extern "C"

@@ -152,6 +152,15 @@ class StateVector:
         N.check(N.lib().sv_apply_circuit(self.h, m.ref(), _dptr(p), C.byref(opts) if opts else None))
         return self
 
+    def plan_info(self, circ, params: Optional[np.ndarray] = None, opts: Optional[N.SvOptions] = None):
+        """(fused blocks, tile passes) the library plans for this circuit."""
+        m = marshal(circ)
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+        nb, npass = C.c_int64(), C.c_int64()
+        N.check(N.lib().sv_plan_info(self.h, m.ref(), _dptr(p), C.byref(opts) if opts else None,
+                                     C.byref(nb), C.byref(npass)))
+        return nb.value, npass.value
+
     # -- observables ---------------------------------------------------------
     def expect(self, terms) -> float:
         arr, nt = pauli_terms(terms)
