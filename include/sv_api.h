@@ -201,6 +201,28 @@ sv_status sv_apply_circuit_batch(sv_state *const *states, int B, const sv_circui
 sv_status sv_expect(sv_state *s, const sv_pauli_term *terms, int n_terms, double *out_host);
 /* out[q] = <Z_q> for q = 0..n-1 in one read pass.  Synchronises. */
 sv_status sv_expect_z_all(sv_state *s, double *out_host);
+/* Same values as sv_expect_z_all, for callers that cannot allocate device
+ * memory: code running while a CUDA graph is being captured, plug-ins whose
+ * host application owns the device allocator, or loops that may not pay an
+ * allocation's implicit synchronisation.  The paper has no counterpart; this
+ * is a service of this library.
+ *   amps_dev:  2^n_qubits amplitudes of `dtype` on the current device,
+ *              256-byte aligned (no state handle needed).
+ *   out_dev:   device array of n_qubits doubles, written with <Z_q>.
+ *   stream:    cudaStream_t the work is enqueued on; the call does not
+ *              synchronise (read out_dev after the stream reaches it).
+ * The call allocates nothing and uses no workspace: its block partial sums
+ * go to one fixed array of 143,360 bytes inside the library, which every
+ * GPU that loads the library keeps until the process exits.  The first call
+ * on a device looks up that array's device address (once per device), so
+ * make it before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race and give wrong results; serialise them.
+ * Errors: SV_EINVAL for null or misaligned pointers, an unknown dtype, or
+ * n_qubits outside [1, 34] (the array's limit); SV_ECUDA if the runtime
+ * cannot resolve the array or launch. */
+sv_status sv_expect_z_all_noalloc(const void *amps_dev, int n_qubits, sv_dtype dtype, double *out_dev,
+                                  void *stream);
 /* norm2 = sum_x |psi_x|^2 (FP64 accumulation).  Synchronises. */
 sv_status sv_norm(sv_state *s, double *norm2_out);
 /* psi := psi / sqrt(sum |psi|^2); optionally returns the old norm^2. */

@@ -86,6 +86,7 @@ def lib():
                                             C.POINTER(dp), C.POINTER(SvOptions)]),
             "sv_expect": (st, [vp, C.POINTER(SvPauliTerm), C.c_int, dp]),
             "sv_expect_z_all": (st, [vp, dp]),
+            "sv_expect_z_all_noalloc": (st, [vp, C.c_int, C.c_int, dp, vp]),
             "sv_norm": (st, [vp, dp]),
             "sv_renormalize": (st, [vp, dp]),
             "sv_sample": (st, [vp, C.c_int64, C.c_uint64, u64p]),

@@ -338,6 +338,59 @@ sv_status launch_z_all(sv_state *s, double *out_dev) {
   return SV_OK;
 }
 
+// ---- <Z_q> without any allocation ------------------------------------------
+// Callers that cannot allocate device memory (code running while a CUDA graph
+// is being captured, hosts whose device allocator belongs to someone else,
+// latency-critical loops where an allocation's implicit synchronisation is
+// not allowed) use sv_expect_z_all_noalloc.  Its per-block partial sums live
+// in the fixed array below, which every GPU that loads this library keeps
+// for the life of the process: kNoAllocBlocks blocks x (kNoAllocMaxQ + 1)
+// doubles = 143,360 bytes.
+constexpr int kNoAllocBlocks = 512;
+constexpr int kNoAllocMaxQ = 34;
+static __device__ __align__(256) double g_zall_scratch[kNoAllocBlocks * (kNoAllocMaxQ + 1)];
+static double *g_zall_scratch_addr[64];   // device address of the array, per device
+
+sv_status zall_noalloc(const void *amps, int n, sv_dtype dt, double *out, cudaStream_t stream) {
+  int dev = 0;
+  SV_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(SV_EUNSUPPORTED, "device ordinal above 63");
+  if (!g_zall_scratch_addr[dev]) {
+    // the array's name is only a host-side handle: ask the runtime for its
+    // address on the current device, once per device
+    void *p = nullptr;
+    SV_CUDA(cudaGetSymbolAddress(&p, g_zall_scratch));
+    g_zall_scratch_addr[dev] = static_cast<double *>(p);
+  }
+  double *partial = g_zall_scratch_addr[dev];
+  int sms = 0;
+  SV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int apu = dt == SV_C64 ? 2 : 1;
+  const uint64_t namps = 1ull << n;
+  const uint64_t chunk_amps = 32ull * 8 * apu;
+  if (namps < chunk_amps) {
+    if (dt == SV_C64)
+      k_zall_small<float><<<1, 256, 0, stream>>>((const float2 *)amps, n, partial);
+    else
+      k_zall_small<double><<<1, 256, 0, stream>>>((const double2 *)amps, n, partial);
+    k_zall_finish<<<1, 64, 0, stream>>>(partial, 1, n, out);
+  } else {
+    const uint64_t nchunks = namps / chunk_amps;
+    const uint64_t wpb = kRedThreads / 32;
+    const uint64_t cap = std::min<uint64_t>((uint64_t)kNoAllocBlocks, (uint64_t)sms * 4);
+    const int g = (int)std::max<uint64_t>(1, std::min<uint64_t>((nchunks + wpb - 1) / wpb, cap));
+    // every block writes all n + 1 of its partial sums, so nothing needs zeroing
+    if (dt == SV_C64)
+      k_zall<float><<<g, kRedThreads, 0, stream>>>((const int4 *)amps, n, nchunks, partial);
+    else
+      k_zall<double><<<g, kRedThreads, 0, stream>>>((const int4 *)amps, n, nchunks, partial);
+    k_zall_finish<<<1, 64, 0, stream>>>(partial, g, n, out);
+  }
+  g_launches += 2;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
 // ---- sampling --------------------------------------------------------------
 constexpr int kChunkBits = 10;  // 1024 amplitudes per CDF chunk
 

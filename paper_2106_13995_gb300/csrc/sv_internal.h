@@ -238,6 +238,7 @@ sv_status launch_norm(sv_state *s, double *out_dev_scalar);
 sv_status launch_expect_group(sv_state *s, uint64_t xmask, const uint64_t *zm, const double *cf,
                               const int *ipow, int nt, double *out_dev);
 sv_status launch_z_all(sv_state *s, double *out_dev);
+sv_status zall_noalloc(const void *amps, int n, sv_dtype dt, double *out, cudaStream_t stream);
 sv_status launch_sample_prepare(sv_state *s);
 sv_status launch_sample_shots(sv_state *s, int64_t shot0, int64_t count, uint64_t seed, uint64_t *out_dev);
 size_t sample_shot_offset(int n);

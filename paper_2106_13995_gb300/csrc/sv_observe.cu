@@ -70,6 +70,17 @@ sv_status sv_expect_z_all(sv_state *s, double *out) {
   return SV_OK;
 }
 
+sv_status sv_expect_z_all_noalloc(const void *amps_dev, int n_qubits, sv_dtype dtype, double *out_dev,
+                                  void *stream) {
+  if (!amps_dev || !out_dev) return set_error(SV_EINVAL, "null device pointer");
+  if (n_qubits < 1 || n_qubits > 34)
+    return set_error(SV_EINVAL, "sv_expect_z_all_noalloc handles 1 to 34 qubits");
+  if (dtype != SV_C64 && dtype != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
+  if ((uintptr_t)amps_dev & 255) return set_error(SV_EINVAL, "amplitudes must be 256-byte aligned");
+  if ((uintptr_t)out_dev & 7) return set_error(SV_EINVAL, "output must be 8-byte aligned");
+  return zall_noalloc(amps_dev, n_qubits, dtype, out_dev, (cudaStream_t)stream);
+}
+
 sv_status sv_norm(sv_state *s, double *out) {
   if (!s || !out) return set_error(SV_EINVAL, "null argument");
   SV_TRY(launch_norm(s, scalars_dev(s)));
