@@ -2,20 +2,32 @@
 //
 // One CTA owns one tile: the 2^m amplitudes whose indices agree outside the
 // pass's qubit set S (the L lowest qubits, contiguous in memory, plus m - L
-// chosen high qubits).  The CTA copies the tile (one or two vectors) into
-// shared memory with 16-byte cp.async, applies the pass's op list there, and
-// writes the tile back, so a whole run of gates costs one read and one write
-// of the state -- the HBM-bound core of the matrix-vector method (paper
+// chosen high qubits).  The CTA reads the tile (one or two vectors) from HBM
+// with 16-byte loads into shared memory, applies the pass's op list there,
+// and writes the tile back, so a whole run of gates costs one read and one
+// write of the state -- the HBM-bound core of the matrix-vector method (paper
 // Sec. II, assumption (a)).  Ops: dense k-qubit blocks with local and
 // out-of-tile controls, diagonal blocks, and the reductions used by the
 // adjoint gradient (Im<lambda|G|psi>, Re<psi|lambda>) and by building
 // lambda = H psi from Pauli strings.
+//
+// Shared-memory layout: amplitude l of the tile lives at sw(l), an XOR
+// swizzle of its low bits by the next bits up.  A gate on low local qubits
+// makes a warp's 32 groups stride through the tile; without the swizzle
+// those strides land on a few banks (up to 8-way conflicts for three low
+// targets), with it every access pattern of the op list spreads over all
+// banks.
 #include "sv_device.cuh"
 #include "sv_internal.h"
 
 namespace sv {
 
 constexpr int kTileMaxThreads = 512;
+
+// swizzled shared-memory slot of tile amplitude l (a bijection on [0, 2^m))
+template <typename R> __device__ __forceinline__ uint32_t sw(uint32_t l);
+template <> __device__ __forceinline__ uint32_t sw<float>(uint32_t l) { return l ^ ((l >> 4) & 15u); }
+template <> __device__ __forceinline__ uint32_t sw<double>(uint32_t l) { return l ^ ((l >> 3) & 7u); }
 
 __device__ __forceinline__ uint64_t tile_base(const TilePass &P, uint64_t t) {
   uint64_t base = 0;
@@ -30,11 +42,15 @@ __device__ __forceinline__ uint64_t spread_hi(const TilePass &P, uint32_t l) {
   return g;
 }
 
-template <typename R, int K>
+// Dense block on K local targets (U row-major complex in global memory,
+// read through L1).  Matrices of 1-2 qubits are held in registers for the
+// whole op; larger ones are read per use, each load serving G groups.
+template <typename R, int K, int G>
 __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
                                          const typename Cx<R>::T *__restrict__ U) {
   using C = typename Cx<R>::T;
   constexpr int D = 1 << K;
+  constexpr bool kRegU = K <= 2;
   uint32_t off[D];
 #pragma unroll
   for (int y = 0; y < D; y++) {
@@ -43,52 +59,41 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
     for (int j = 0; j < K; j++) o |= (uint32_t)((y >> j) & 1) << op.t[j];
     off[y] = o;
   }
+  C ur[kRegU ? D * D : 1];
+  if constexpr (kRegU) {
+#pragma unroll
+    for (int e = 0; e < D * D; e++) ur[e] = __ldg(&U[e]);
+  }
   const uint32_t fixed = off[D - 1] | op.lcmask;
   const uint32_t ngroups = 1u << (m - __popc(fixed));
-  if constexpr (K <= 2) {
-    C u[D * D];
+  const uint32_t step = blockDim.x * G;
+  for (uint32_t g0 = threadIdx.x; g0 < ngroups; g0 += step) {
+    uint32_t i0[G];
+    bool ok[G];
+    C x[G][D];
 #pragma unroll
-    for (int e = 0; e < D * D; e++) u[e] = U[e];
-    for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-      const uint32_t i0 = ins0_mask(g, fixed) | op.lcmask;
-      C x[D];
+    for (int h = 0; h < G; h++) {
+      const uint32_t g = g0 + h * blockDim.x;
+      ok[h] = g < ngroups;
+      i0[h] = ins0_mask(ok[h] ? g : 0, fixed) | op.lcmask;
 #pragma unroll
-      for (int y = 0; y < D; y++) x[y] = v[i0 + off[y]];
-#pragma unroll
-      for (int r = 0; r < D; r++) {
-        C a = czero<C>();
-#pragma unroll
-        for (int y = 0; y < D; y++) a = cfma(u[r * D + y], x[y], a);
-        v[i0 + off[r]] = a;
-      }
+      for (int y = 0; y < D; y++) x[h][y] = v[sw<R>(i0[h] + off[y])];
     }
-  } else {
-    for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-      const uint32_t i0 = ins0_mask(g, fixed) | op.lcmask;
-      C x[D];
+#pragma unroll(kRegU ? D : 1)
+    for (int r = 0; r < D; r++) {
+      C a[G];
 #pragma unroll
-      for (int y = 0; y < D; y++) x[y] = v[i0 + off[y]];
-#pragma unroll 1
-      for (int r = 0; r < D; r++) {
-        C a = czero<C>();
+      for (int h = 0; h < G; h++) a[h] = czero<C>();
 #pragma unroll
-        for (int y = 0; y < D; y++) a = cfma(__ldg(&U[r * D + y]), x[y], a);
-        v[i0 + off[r]] = a;
+      for (int y = 0; y < D; y++) {
+        const C u = kRegU ? ur[(r * D + y) % (kRegU ? D * D : 1)] : __ldg(&U[r * D + y]);
+#pragma unroll
+        for (int h = 0; h < G; h++) a[h] = cfma(u, x[h][y], a[h]);
       }
+#pragma unroll
+      for (int h = 0; h < G; h++)
+        if (ok[h]) v[sw<R>(i0[h] + off[r])] = a[h];
     }
-  }
-}
-
-template <typename R>
-__device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
-                                        const typename Cx<R>::T *__restrict__ d) {
-  using C = typename Cx<R>::T;
-  const uint32_t ngroups = 1u << (m - __popc(op.lcmask));
-  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-    const uint32_t l = ins0_mask(g, op.lcmask) | op.lcmask;
-    uint32_t r = 0;
-    for (int j = 0; j < op.k; j++) r |= ((l >> op.t[j]) & 1u) << j;
-    v[l] = cmul(__ldg(&d[r]), v[l]);
   }
 }
 
@@ -98,7 +103,20 @@ __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m
 template <typename R, int K>
 __device__ __noinline__ void dense_op_big(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
                                           const typename Cx<R>::T *__restrict__ U) {
-  dense_op<R, K>(v, m, op, U);
+  dense_op<R, K, 1>(v, m, op, U);
+}
+
+template <typename R>
+__device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
+                                        const typename Cx<R>::T *__restrict__ d) {
+  const uint32_t ngroups = 1u << (m - __popc(op.lcmask));
+  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const uint32_t l = ins0_mask(g, op.lcmask) | op.lcmask;
+    uint32_t r = 0;
+    for (int j = 0; j < op.k; j++) r |= ((l >> op.t[j]) & 1u) << j;
+    const uint32_t p = sw<R>(l);
+    v[p] = cmul(__ldg(&d[r]), v[p]);
+  }
 }
 
 template <typename R>
@@ -109,9 +127,9 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
     return;
   }
   switch (op.k) {
-    case 1: dense_op<R, 1>(v, m, op, U); break;
-    case 2: dense_op<R, 2>(v, m, op, U); break;
-    case 3: dense_op<R, 3>(v, m, op, U); break;
+    case 1: dense_op<R, 1, 2>(v, m, op, U); break;
+    case 2: dense_op<R, 2, 1>(v, m, op, U); break;
+    case 3: dense_op<R, 3, sizeof(R) == 4 ? 2 : 1>(v, m, op, U); break;
     case 4: dense_op_big<R, 4>(v, m, op, U); break;
     case 5: dense_op_big<R, 5>(v, m, op, U); break;
     default: dense_op_big<R, 6>(v, m, op, U); break;
@@ -140,7 +158,8 @@ __device__ void grad_op(const typename Cx<R>::T *__restrict__ psi,
   R part = 0;
   for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
     const uint32_t l0 = ins0(g, t), l1 = l0 | bit;
-    const C a0 = psi[l0], a1 = psi[l1], b0 = lam[l0], b1 = lam[l1];
+    const uint32_t p0 = sw<R>(l0), p1 = sw<R>(l1);
+    const C a0 = psi[p0], a1 = psi[p1], b0 = lam[p0], b1 = lam[p1];
     switch (op.gen) {
       case 1:  // X
         part += imdot(b0, a1) + imdot(b1, a0);
@@ -161,6 +180,32 @@ __device__ void grad_op(const typename Cx<R>::T *__restrict__ psi,
   block_acc<R>(part, acc + op.slot);
 }
 
+// 16-byte unit u of the tile <-> shared memory (swizzled amplitude slots)
+template <typename R> struct Unit;
+template <> struct Unit<float> {
+  static constexpr uint32_t APU = 2;
+  __device__ static void put(float2 *v, uint32_t l, int4 raw) {
+    const float4 f = *reinterpret_cast<const float4 *>(&raw);
+    v[sw<float>(l)] = make_float2(f.x, f.y);
+    v[sw<float>(l + 1)] = make_float2(f.z, f.w);
+  }
+  __device__ static int4 get(const float2 *v, uint32_t l) {
+    const float2 a = v[sw<float>(l)], b = v[sw<float>(l + 1)];
+    const float4 f = make_float4(a.x, a.y, b.x, b.y);
+    return *reinterpret_cast<const int4 *>(&f);
+  }
+};
+template <> struct Unit<double> {
+  static constexpr uint32_t APU = 1;
+  __device__ static void put(double2 *v, uint32_t l, int4 raw) {
+    v[sw<double>(l)] = *reinterpret_cast<const double2 *>(&raw);
+  }
+  __device__ static int4 get(const double2 *v, uint32_t l) {
+    const double2 a = v[sw<double>(l)];
+    return *reinterpret_cast<const int4 *>(&a);
+  }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_constant__ TilePass P) {
   using C = typename Cx<R>::T;
@@ -173,17 +218,33 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_consta
   C *g0 = reinterpret_cast<C *>(P.tbl0 ? P.tbl0[b] : P.v0);
   C *g1 = P.nvec > 1 ? reinterpret_cast<C *>(P.tbl1 ? P.tbl1[b] : P.v1) : nullptr;
 
-  constexpr uint32_t APU = 16 / sizeof(C);  // amplitudes per 16-byte unit
-  const uint32_t nunits = TS / APU;
+  using UN = Unit<R>;
+  const uint32_t nunits = TS / UN::APU;
   const uint32_t segmask = (1u << P.L) - 1;
   const bool load1 = P.nvec > 1 && !(P.flags & 1u);
-  for (uint32_t u = threadIdx.x; u < nunits; u += blockDim.x) {
-    const uint32_t l = u * APU;
-    const uint64_t g = base | (l & segmask) | spread_hi(P, l);
-    cp_async16(&v0[l], &g0[g]);
-    if (load1) cp_async16(&v1[l], &g1[g]);
+  // loads: four 16-byte units in flight per thread before any shared store
+  constexpr int BATCH = 4;
+  for (uint32_t u0 = threadIdx.x; u0 < nunits; u0 += BATCH * blockDim.x) {
+    int4 r0[BATCH], r1[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; j++) {
+      const uint32_t u = u0 + j * blockDim.x;
+      if (u < nunits) {
+        const uint32_t l = u * UN::APU;
+        const uint64_t g = base | (l & segmask) | spread_hi(P, l);
+        r0[j] = __ldcs(reinterpret_cast<const int4 *>(&g0[g]));
+        if (load1) r1[j] = __ldcs(reinterpret_cast<const int4 *>(&g1[g]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BATCH; j++) {
+      const uint32_t u = u0 + j * blockDim.x;
+      if (u < nunits) {
+        UN::put(v0, u * UN::APU, r0[j]);
+        if (load1) UN::put(v1, u * UN::APU, r1[j]);
+      }
+    }
   }
-  cp_async_wait_all();
 
   const C *mats = reinterpret_cast<const C *>(P.mats);
   const C *pmats = P.pmats ? reinterpret_cast<const C *>(P.pmats) + (size_t)b * P.pmats_stride : nullptr;
@@ -221,8 +282,8 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_consta
         for (uint32_t l = threadIdx.x; l < TS; l += blockDim.x) {
           const int s = (__popc(l & zl) + tsign) & 1;
           const R sr = s ? -fr : fr, si = s ? -fi : fi;
-          const C a = v0[l];
-          C &dst = v1[l ^ xm];
+          const C a = v0[sw<R>(l)];
+          C &dst = v1[sw<R>(l ^ xm)];
           dst.x += sr * a.x - si * a.y;
           dst.y += sr * a.y + si * a.x;
         }
@@ -234,7 +295,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_consta
       case TOP_DOT: {
         R part = 0;
         for (uint32_t l = threadIdx.x; l < TS; l += blockDim.x) {
-          const C a = v0[l], c = v1[l];
+          const C a = v0[l], c = v1[l];   // same slot in both vectors: the swizzle cancels
           part += a.x * c.x + a.y * c.y;
         }
         block_acc<R>(part, acc + op.slot);
@@ -247,10 +308,10 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_consta
   __syncthreads();
   const bool store0 = !(P.flags & 2u), store1 = P.nvec > 1 && !(P.flags & 4u);
   for (uint32_t u = threadIdx.x; u < nunits; u += blockDim.x) {
-    const uint32_t l = u * APU;
+    const uint32_t l = u * UN::APU;
     const uint64_t g = base | (l & segmask) | spread_hi(P, l);
-    if (store0) __stcs(reinterpret_cast<int4 *>(&g0[g]), *reinterpret_cast<const int4 *>(&v0[l]));
-    if (store1) __stcs(reinterpret_cast<int4 *>(&g1[g]), *reinterpret_cast<const int4 *>(&v1[l]));
+    if (store0) __stcs(reinterpret_cast<int4 *>(&g0[g]), UN::get(v0, l));
+    if (store1) __stcs(reinterpret_cast<int4 *>(&g1[g]), UN::get(v1, l));
   }
 }
 
@@ -263,6 +324,7 @@ int tile_threads(int m, sv_dtype dt) {
 }
 
 size_t tile_smem(sv_dtype dt, int m, int nvec) { return (size_t)nvec * ((size_t)1 << m) * amp_bytes(dt); }
+
 
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
   static bool attr_set[2][64] = {};

@@ -43,7 +43,7 @@ size_t red_bytes(int n) {
 Opts resolve(const sv_state *s, const sv_options *o, int nvec) {
   Opts r;
   r.fusion_k = (o && o->fusion_k > 0) ? o->fusion_k : 3;
-  r.tile_m = (o && o->tile_m > 0) ? o->tile_m : (s->dt == SV_C64 ? 13 : 12) - (nvec - 1);
+  r.tile_m = (o && o->tile_m > 0) ? o->tile_m : (s->dt == SV_C64 ? 12 : 12) - (nvec - 1);
   r.L = s->dt == SV_C64 ? 4 : 3;
   r.prec = o ? o->prec : SV_PREC_PLAIN;
   r.mode = o ? o->mode : SV_MODE_TILED;
