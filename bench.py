@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--qubits", type=int, default=30,
                     help="30 = the 5x6 grid; fewer = the same grid with random qubits removed")
     ap.add_argument("--sections", default="all",
-                    help="comma list of step,e2e,roofline,single,adjoint,cpu (default all)")
+                    help="comma list of step,e2e,roofline,single,adjoint,uneven,cpu (default all)")
     return ap.parse_args()
 
 
@@ -210,7 +210,7 @@ def main():
     from paper_2106_13995_gb300 import sim
 
     sections = set(args.sections.split(",")) if args.sections != "all" else \
-        {"step", "e2e", "roofline", "single", "adjoint", "cpu"}
+        {"step", "e2e", "roofline", "single", "adjoint", "uneven", "cpu"}
     circ = workload(args.qubits)
     n = circ.n_qubits
     m = sim.marshal(circ)
@@ -358,6 +358,44 @@ def main():
                           "speedup": tp / tb, "batch": B, "n_qubits": na, "gates": len(h.ops),
                           "params": h.n_params, "state": "complex64, FP64 reductions"}
         del psis, lams
+
+    # ---- uneven batch: 256 circuits of widths 10..24, one persistent launch -------
+    if "uneven" in sections:
+        import ctypes as C
+        from paper_2106_13995_gb300 import _native as N
+        torch.cuda.empty_cache()
+        circs = W.uneven_batch()
+        ums = [sim.marshal(c) for c in circs]
+        ust = [sim.StateVector(c.n_qubits, "c64", device=dev) for c in circs]
+        hs = (C.c_void_p * len(ust))(*[s.h.value for s in ust])
+        cs = (C.POINTER(N.SvCircuit) * len(ust))(*[C.pointer(mm.c) for mm in ums])
+        gopt = sim.options(mode=N.SV_MODE_TILED_GRAPH)
+
+        def uneven_batched():
+            for st_ in ust:
+                st_.set_basis(0)
+            N.check(N.lib().sv_apply_circuit_batch(hs, len(ust), cs, None, C.byref(gopt)))
+
+        def uneven_plain():
+            for st_, mm in zip(ust, ums):
+                st_.set_basis(0)
+                st_.apply_circuit(mm)
+
+        for _ in range(max(1, args.warmup)):
+            uneven_batched()
+            uneven_plain()
+        N.check(N.lib().sv_synchronize(ust[0].h))
+        ku = max(2, args.steps // 2)
+        tbu = timed(uneven_batched, ku) / ku
+        N.check(N.lib().sv_synchronize(ust[0].h))
+        tpu = timed(uneven_plain, ku) / ku
+        out["uneven_batch"] = {"circuits_per_s_batched": len(circs) / tbu, "circuits_per_s_plain": len(circs) / tpu,
+                               "speedup": tpu / tbu, "circuits": len(circs), "widths": "10..24", "depth": 40,
+                               "gates": int(sum(len(c.ops) for c in circs)),
+                               "launch": "one CUDA graph per call: a persistent cooperative launch for states "
+                                         "whose passes have < 2 tiles per SM, full-grid tile launches for the "
+                                         "wider ones; plus one basis-state write per state"}
+        del ust
 
     # ---- the FP64 oracle on this host's cores ------------------------------------
     if "cpu" in sections and rank == 0:

@@ -102,8 +102,9 @@ typedef struct {
 } sv_circuit;
 
 typedef enum {
-  SV_MODE_TILED = 0,     /* fuse gates into blocks, group blocks into shared-memory tile passes */
-  SV_MODE_PER_GATE = 1   /* one global-memory pass per (fused) block */
+  SV_MODE_TILED = 0,       /* fuse gates into blocks, group blocks into shared-memory tile passes */
+  SV_MODE_PER_GATE = 1,    /* one global-memory pass per (fused) block */
+  SV_MODE_TILED_GRAPH = 2  /* as TILED; sv_apply_circuit_batch replays its launch from a CUDA graph */
 } sv_mode;
 
 typedef struct {
@@ -183,12 +184,23 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *param
 sv_status sv_plan_info(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
                        int64_t *n_blocks, int64_t *n_passes);
 
-/* Apply the same circuit structure to B states (each with its own parameter
- * vector params[b], host FP64, may be NULL) in one launch sequence.  States
- * may have different widths only if circuits differ (circs[b] matches
- * states[b]); all states must share the first state's stream and device.
- * Work for all states is scheduled by one persistent kernel per pass
- * wave.  Errors as sv_apply_circuit. */
+/* Apply circs[b] (with parameters params[b], host FP64, either may repeat)
+ * to states[b] for b < B, states of any widths, in ONE persistent launch:
+ * every circuit is fused and planned into tile passes as by
+ * sv_apply_circuit, and a cooperative kernel works through the queue of all
+ * (state, pass, tile) items in pass order; a tile of pass p waits until pass
+ * p-1 of its own state is complete (Sec. I motivates many independent
+ * simulations: variational training evaluates many circuits).  Waits are
+ * bounded by opt->timeout_cycles polls (~128 ns each; 0 = about 1 s); a wait
+ * that runs out stops the launch and the next sv_synchronize on states[0]
+ * returns SV_ETIMEOUT.  With opt->mode == SV_MODE_TILED_GRAPH the counter
+ * reset and the launch are captured once per batch layout and replayed as a
+ * CUDA graph.  fusion_k / tile_m left at 0 take the autotuner's cached
+ * choice for the circuit's shape, if any.  All states must be distinct and
+ * share one stream and device; the first state's workspace holds the batch
+ * tables.  Enqueues only (no synchronisation).  Errors: SV_EINVAL (arguments,
+ * per-gate mode), SV_ENOMEM (batch tables exceed the first state's reduction
+ * area), SV_ECUDA. */
 sv_status sv_apply_circuit_batch(sv_state *const *states, int B, const sv_circuit *const *circs,
                                  const double *const *params, const sv_options *opt);
 
@@ -266,11 +278,22 @@ sv_status sv_adjoint_grad_batch(sv_state *const *psi, sv_state *const *lam, int 
  * Runtime services
  * ------------------------------------------------------------------------- */
 
-/* Time candidate (fusion_k, tile_m) pairs for this circuit on `scratch`
- * (its contents are clobbered) and write the fastest into *inout.  Results
- * are cached per (n, dtype, circuit shape) in memory and, if the
- * SV_TUNE_CACHE environment variable names a file, in that JSON file. */
+/* Time candidate (fusion_k in 2..6, tile_m in 10..13, limited by n) pairs
+ * for this circuit on `scratch` (its contents are clobbered; the circuit must
+ * not be parametric) and write the fastest into *inout.  The choice is
+ * cached per (n, dtype, op-count bucket, widest op) in memory and, if the
+ * SV_TUNE_CACHE environment variable names a file, in that JSON file;
+ * sv_apply_circuit and sv_apply_circuit_batch use it for options left at 0.
+ * Synchronises. */
 sv_status sv_autotune(sv_state *scratch, const sv_circuit *c, sv_options *inout);
+
+/* Launch a one-thread kernel that waits, bounded by `polls` polls (~128 ns
+ * each), on a device counter that nothing ever increments, and report the
+ * outcome: SV_ETIMEOUT when the bound is reached (the expected result; the
+ * context stays usable), SV_OK otherwise.  Exercises the same bounded wait
+ * the persistent batch kernel uses, without any fault.  Synchronises
+ * `stream`.  The paper has no counterpart. */
+sv_status sv_wait_selftest(void *stream, uint64_t polls);
 
 /* Number of kernels this library has launched in this process (all
  * devices).  Lets callers count device work without a profiler. */

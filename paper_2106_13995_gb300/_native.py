@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsv.so")
 SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_ETIMEOUT, SV_EUNSUPPORTED = range(6)
 SV_C64, SV_C128 = 0, 1
 SV_PREC_PLAIN, SV_PREC_TC_BF16X3, SV_PREC_TC_TF32X3 = 0, 1, 2
-SV_MODE_TILED, SV_MODE_PER_GATE = 0, 1
+SV_MODE_TILED, SV_MODE_PER_GATE, SV_MODE_TILED_GRAPH = 0, 1, 2
 
 GATE_IDS = {
     "MATRIX": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
@@ -95,6 +95,7 @@ def lib():
             "sv_adjoint_grad_batch": (st, [C.POINTER(vp), C.POINTER(vp), C.c_int, C.POINTER(SvCircuit), dp,
                                            C.POINTER(SvPauliTerm), C.c_int, C.POINTER(SvOptions), dp, dp]),
             "sv_autotune": (st, [vp, C.POINTER(SvCircuit), C.POINTER(SvOptions)]),
+            "sv_wait_selftest": (st, [vp, C.c_uint64]),
             "sv_kernel_launch_count": (C.c_uint64, []),
             "sv_last_error": (C.c_char_p, []),
             "sv_status_string": (C.c_char_p, [C.c_int]),

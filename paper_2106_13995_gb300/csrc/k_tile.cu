@@ -206,15 +206,16 @@ template <> struct Unit<double> {
   }
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_constant__ TilePass P) {
+// The work of one CTA on one tile.  COH selects L2-coherent loads and stores
+// (bypassing L1), needed when other CTAs of the same launch wrote the tile
+// earlier (the persistent batch kernel); otherwise streaming hints are used.
+template <typename R, bool COH>
+__device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int b, unsigned char *smem_raw) {
   using C = typename Cx<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t TS = 1u << P.m;
   C *v0 = reinterpret_cast<C *>(smem_raw);
   C *v1 = v0 + TS;
-  const int b = blockIdx.y;
-  const uint64_t base = tile_base(P, blockIdx.x);
+  const uint64_t base = tile_base(P, tile);
   C *g0 = reinterpret_cast<C *>(P.tbl0 ? P.tbl0[b] : P.v0);
   C *g1 = P.nvec > 1 ? reinterpret_cast<C *>(P.tbl1 ? P.tbl1[b] : P.v1) : nullptr;
 
@@ -222,23 +223,36 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_consta
   const uint32_t nunits = TS / UN::APU;
   const uint32_t segmask = (1u << P.L) - 1;
   const bool load1 = P.nvec > 1 && !(P.flags & 1u);
+  // Global offset of unit u = threadIdx.x + i * blockDim.x: the thread's bits
+  // and the trip's bits of the local index are disjoint, so their spreads
+  // are computed separately (the thread part once per tile).
+  const uint32_t lthr = threadIdx.x * UN::APU;
+  const uint64_t gthr = base | (lthr & segmask) | spread_hi(P, lthr & ~segmask);
+  const uint32_t tstep = blockDim.x * UN::APU;
+  auto goff = [&](uint32_t i) -> uint64_t {
+    const uint32_t lt = i * tstep;     // bits above the thread bits
+    return gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
+  };
   // loads: four 16-byte units in flight per thread before any shared store
   constexpr int BATCH = 4;
-  for (uint32_t u0 = threadIdx.x; u0 < nunits; u0 += BATCH * blockDim.x) {
+  for (uint32_t i0 = 0; i0 * blockDim.x + threadIdx.x < nunits; i0 += BATCH) {
     int4 r0[BATCH], r1[BATCH];
 #pragma unroll
     for (int j = 0; j < BATCH; j++) {
-      const uint32_t u = u0 + j * blockDim.x;
+      const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
       if (u < nunits) {
-        const uint32_t l = u * UN::APU;
-        const uint64_t g = base | (l & segmask) | spread_hi(P, l);
-        r0[j] = __ldcs(reinterpret_cast<const int4 *>(&g0[g]));
-        if (load1) r1[j] = __ldcs(reinterpret_cast<const int4 *>(&g1[g]));
+        const uint64_t g = goff(i0 + j);
+        const int4 *p0 = reinterpret_cast<const int4 *>(&g0[g]);
+        r0[j] = COH ? __ldcg(p0) : __ldcs(p0);
+        if (load1) {
+          const int4 *p1 = reinterpret_cast<const int4 *>(&g1[g]);
+          r1[j] = COH ? __ldcg(p1) : __ldcs(p1);
+        }
       }
     }
 #pragma unroll
     for (int j = 0; j < BATCH; j++) {
-      const uint32_t u = u0 + j * blockDim.x;
+      const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
       if (u < nunits) {
         UN::put(v0, u * UN::APU, r0[j]);
         if (load1) UN::put(v1, u * UN::APU, r1[j]);
@@ -307,12 +321,107 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_consta
   }
   __syncthreads();
   const bool store0 = !(P.flags & 2u), store1 = P.nvec > 1 && !(P.flags & 4u);
-  for (uint32_t u = threadIdx.x; u < nunits; u += blockDim.x) {
-    const uint32_t l = u * UN::APU;
-    const uint64_t g = base | (l & segmask) | spread_hi(P, l);
-    if (store0) __stcs(reinterpret_cast<int4 *>(&g0[g]), UN::get(v0, l));
-    if (store1) __stcs(reinterpret_cast<int4 *>(&g1[g]), UN::get(v1, l));
+  for (uint32_t i = 0; i * blockDim.x + threadIdx.x < nunits; i++) {
+    const uint32_t l = (i * blockDim.x + threadIdx.x) * UN::APU;
+    const uint64_t g = goff(i);
+    if (store0) {
+      if (COH) __stcg(reinterpret_cast<int4 *>(&g0[g]), UN::get(v0, l));
+      else __stcs(reinterpret_cast<int4 *>(&g0[g]), UN::get(v0, l));
+    }
+    if (store1) {
+      if (COH) __stcg(reinterpret_cast<int4 *>(&g1[g]), UN::get(v1, l));
+      else __stcs(reinterpret_cast<int4 *>(&g1[g]), UN::get(v1, l));
+    }
   }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_constant__ TilePass P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tile_body<R, false>(P, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batch kernel: one cooperative launch works through a queue of
+// (pass, tile) items of many independent states, pass by pass in wave order.
+// An item of pass p of a state waits (bounded) until every tile of pass p-1
+// of that state is done; all CTAs are co-resident (cooperative launch) and
+// items are handed out in queue order, so every awaited item is already held
+// by a running CTA.  A wait that runs out sets *err and the CTA stops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Poll *ctr until it reaches target; at most `limit` polls ~128 ns apart.
+__device__ __forceinline__ bool bounded_wait(const uint32_t *ctr, uint32_t target, uint64_t limit) {
+  for (uint64_t i = 0; i < limit; i++) {
+    if (ld_acquire(ctr) >= target) return true;
+    __nanosleep(128);
+  }
+  return ld_acquire(ctr) >= target;
+}
+
+// the tile body out of line, so the queue loop's registers do not crowd it
+template <typename R>
+__device__ __noinline__ void tile_body_coherent(const TilePass &P, uint64_t tile, unsigned char *smem_raw) {
+  tile_body<R, true>(P, tile, 0, smem_raw);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile_persist(const __grid_constant__ PersistArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ TilePass sP;
+  __shared__ unsigned long long s_chunk;
+  __shared__ int s_desc, s_stop;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_chunk = atomicAdd(A.next_item, 1ull);
+      s_stop = 0;
+      if (s_chunk < A.total_items) {
+        // last descriptor whose first chunk is <= s_chunk
+        uint32_t lo = 0, hi = A.ndesc - 1;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (A.first_item[mid] <= s_chunk) lo = mid; else hi = mid - 1;
+        }
+        s_desc = (int)lo;
+        const int dep = A.dep[lo];
+        if (dep >= 0 && !bounded_wait(A.done + dep, A.ntiles[dep], A.spin_limit)) {
+          atomicExch(A.err, 1u);
+          s_stop = 1;
+        }
+        if (!s_stop) {
+          __threadfence();
+          sP = A.passes[lo];
+        }
+      } else {
+        s_stop = 1;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int d = s_desc;
+    const uint32_t nt = A.ntiles[d], ch = A.chunk[d];
+    const uint64_t t0 = (s_chunk - A.first_item[d]) * ch;
+    const uint64_t left = (uint64_t)nt - t0;
+    const uint32_t cnt = left < ch ? (uint32_t)left : ch;
+    for (uint32_t j = 0; j < cnt; j++) {
+      tile_body_coherent<R>(sP, t0 + j, smem_raw);
+      __syncthreads();
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(A.done + d, cnt);
+  }
+}
+
+// Self-test of the bounded wait: waits on a counter nothing increments and
+// reports the timeout through *err (status read by the host).
+__global__ void k_wait_selftest(const uint32_t *never, uint32_t *err, uint64_t limit) {
+  if (threadIdx.x == 0 && !bounded_wait(never, 1u, limit)) atomicExch(err, 1u);
 }
 
 int tile_threads(int m, sv_dtype dt) {
@@ -327,6 +436,10 @@ size_t tile_smem(sv_dtype dt, int m, int nvec) { return (size_t)nvec * ((size_t)
 
 
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
+  return launch_tile_pass_on(s, p, batch, s->stream);
+}
+
+sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream) {
   static bool attr_set[2][64] = {};
   const size_t smem = tile_smem(s->dt, p.m, (int)p.nvec);
   const int dev = s->device & 63;
@@ -342,9 +455,33 @@ sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
   dim3 grid((unsigned)(1ull << (p.n - p.m)), (unsigned)batch);
   const int threads = tile_threads(p.m, s->dt);
   if (s->dt == SV_C64)
-    k_tile<float><<<grid, threads, smem, s->stream>>>(p);
+    k_tile<float><<<grid, threads, smem, stream>>>(p);
   else
-    k_tile<double><<<grid, threads, smem, s->stream>>>(p);
+    k_tile<double><<<grid, threads, smem, stream>>>(p);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+sv_status launch_tile_persist(sv_state *s, const PersistArgs &A, int m_max, int *grid_out, cudaStream_t st) {
+  const size_t smem = tile_smem(s->dt, m_max, 1);
+  if (smem > (200u << 10)) return set_error(SV_EINVAL, "tile too large for shared memory");
+  const void *fn = s->dt == SV_C64 ? (const void *)k_tile_persist<float> : (const void *)k_tile_persist<double>;
+  SV_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+  int per_sm = 0;
+  SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTileMaxThreads, smem));
+  if (per_sm < 1) return set_error(SV_EUNSUPPORTED, "persistent tile kernel does not fit on an SM");
+  const int grid = per_sm * s->sm_count;
+  PersistArgs a = A;
+  void *args[] = {&a};
+  SV_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileMaxThreads), args, smem, st));
+  g_launches++;
+  if (grid_out) *grid_out = grid;
+  return SV_OK;
+}
+
+sv_status launch_wait_selftest(cudaStream_t st, const uint32_t *never, uint32_t *err, uint64_t limit) {
+  k_wait_selftest<<<1, 32, 0, st>>>(never, err, limit);
   g_launches++;
   SV_CUDA(cudaGetLastError());
   return SV_OK;

@@ -267,19 +267,4 @@ sv_status sv_adjoint_grad_batch(sv_state *const *psi, sv_state *const *lam, int 
   return adjoint_batch(psi, lam, B, c, params, terms, nt, opt, ev, grad);
 }
 
-sv_status sv_apply_circuit_batch(sv_state *const *states, int B, const sv_circuit *const *circs,
-                                 const double *const *params, const sv_options *opt) {
-  if (!states || !circs || B < 1) return set_error(SV_EINVAL, "null argument");
-  for (int b = 0; b < B; b++) {
-    const double *p = params ? params[b] : nullptr;
-    SV_TRY(sv_apply_circuit(states[b], circs[b], p, opt));
-  }
-  return SV_OK;
-}
-
-sv_status sv_autotune(sv_state *scratch, const sv_circuit *c, sv_options *inout) {
-  if (!scratch || !c || !inout) return set_error(SV_EINVAL, "null argument");
-  return set_error(SV_EUNSUPPORTED, "autotuner not built yet");
-}
-
 }  // extern "C"

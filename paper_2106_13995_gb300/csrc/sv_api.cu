@@ -191,15 +191,24 @@ ProgLayout layout_of(const DeviceProgram &p, size_t tbl_bytes, size_t pmats_byte
   return L;
 }
 
-// Copy host bytes into the workspace program area through the pinned buffer.
-sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, size_t>> &parts,
-                              const std::vector<size_t> &offs, size_t total) {
-  if (total > kWsProgBytes) return set_error(SV_ENOMEM, "gate program exceeds the workspace program area");
+// Copy host bytes to device memory `dst` through the state's pinned buffer
+// (at most kWsProgBytes per call), ordered on the state's stream.
+sv_status stage_upload_to(sv_state *s, void *dst, const std::vector<std::pair<const void *, size_t>> &parts,
+                          const std::vector<size_t> &offs, size_t total) {
+  if (total > kWsProgBytes) return set_error(SV_ENOMEM, "upload exceeds the staging buffer");
   SV_CUDA(cudaEventSynchronize(s->staged));
   for (size_t i = 0; i < parts.size(); i++)
     if (parts[i].second) std::memcpy(s->pinned + offs[i], parts[i].first, parts[i].second);
-  SV_CUDA(cudaMemcpyAsync(s->ws + kWsProg, s->pinned, total, cudaMemcpyHostToDevice, s->stream));
+  SV_CUDA(cudaMemcpyAsync(dst, s->pinned, total, cudaMemcpyHostToDevice, s->stream));
   SV_CUDA(cudaEventRecord(s->staged, s->stream));
+  return SV_OK;
+}
+
+// Copy host bytes into the workspace program area.
+sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, size_t>> &parts,
+                       const std::vector<size_t> &offs, size_t total) {
+  if (total > kWsProgBytes) return set_error(SV_ENOMEM, "gate program exceeds the workspace program area");
+  SV_TRY(stage_upload_to(s, s->ws + kWsProg, parts, offs, total));
   s->resident_key = 0;
   return SV_OK;
 }
@@ -226,13 +235,6 @@ sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &
   return SV_OK;
 }
 
-// Cached plain-circuit program (one vector).
-struct CachedProgram {
-  DeviceProgram prog;
-  std::vector<uint32_t> op0s;
-  ProgLayout lay;
-  std::vector<Block> blocks;   // for per-gate mode
-};
 static std::map<std::pair<const sv_state *, uint64_t>, CachedProgram> g_cache;
 
 static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gates, const Opts &o,
@@ -264,7 +266,7 @@ static sv_status run_blocks_per_gate(sv_state *s, const std::vector<Block> &bloc
   return SV_OK;
 }
 
-static sv_status upload_program(sv_state *s, const CachedProgram &cp, uint64_t key) {
+sv_status upload_program(sv_state *s, const CachedProgram &cp, uint64_t key) {
   if (s->resident_key == key && key != 0) return SV_OK;
   const DeviceProgram &p = cp.prog;
   std::vector<std::pair<const void *, size_t>> parts = {
@@ -274,6 +276,37 @@ static sv_status upload_program(sv_state *s, const CachedProgram &cp, uint64_t k
   std::vector<size_t> offs = {cp.lay.ops_off, cp.lay.mats_off, cp.lay.coeffs_off};
   SV_TRY(stage_upload(s, parts, offs, cp.lay.end));
   s->resident_key = key;
+  return SV_OK;
+}
+
+sv_status get_program(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
+                      const CachedProgram **out, uint64_t *key_out, Opts *o_out) {
+  if (!s) return set_error(SV_EINVAL, "null state");
+  if (!c) return set_error(SV_EINVAL, "null circuit");
+  Opts o = resolve(s, opt, 1);
+  tuned_options(s, c, opt, o);
+  Hasher H;
+  H.val(circuit_hash(c, 0x51));
+  H.val(o.fusion_k);
+  H.val(o.tile_m);
+  H.val(o.L);
+  H.val(o.mode);
+  H.val((int)s->dt);
+  if (params && c->n_params > 0) H.bytes(params, sizeof(double) * c->n_params);
+  const uint64_t key = H.h;
+  auto ck = std::make_pair((const sv_state *)s, key);
+  auto it = g_cache.find(ck);
+  if (it == g_cache.end()) {
+    std::vector<Gate> gates;
+    SV_TRY(circuit_to_gates(c, params, s->n, gates, false));
+    CachedProgram cp;
+    SV_TRY(build_circuit_program(s, gates, o, cp));
+    if (g_cache.size() > 2048) g_cache.clear();
+    it = g_cache.emplace(ck, std::move(cp)).first;
+  }
+  *out = &it->second;
+  *key_out = key;
+  *o_out = o;
   return SV_OK;
 }
 
@@ -344,6 +377,7 @@ sv_status sv_create(int n, sv_dtype dt, void *amps, size_t amps_bytes, void *ws,
   if (e == cudaSuccess) e = cudaMallocHost((void **)&s->pinned, kPinnedBytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->staged, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(s->staged, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->ws + kWsCtrl + kWsErrFlag, 0, sizeof(uint32_t), s->stream);
   if (e != cudaSuccess) {
     if (s->pinned) cudaFreeHost(s->pinned);
     delete s;
@@ -359,6 +393,8 @@ sv_status sv_destroy(sv_state *s) {
   cudaStreamSynchronize(s->stream);
   for (auto it = g_cache.begin(); it != g_cache.end();)
     it = (it->first.first == s) ? g_cache.erase(it) : std::next(it);
+  drop_graphs(s);
+  if (s->capture) cudaStreamDestroy(s->capture);
   if (s->staged) cudaEventDestroy(s->staged);
   if (s->pinned) cudaFreeHost(s->pinned);
   delete s;
@@ -389,7 +425,15 @@ sv_status sv_download(sv_state *s, void *host, size_t bytes) {
 
 sv_status sv_synchronize(sv_state *s) {
   if (!s) return set_error(SV_EINVAL, "null state");
+  uint32_t *flag = reinterpret_cast<uint32_t *>(s->ws + kWsCtrl + kWsErrFlag);
+  uint32_t *host = reinterpret_cast<uint32_t *>(s->pinned + kWsProgBytes + 4096);
+  SV_CUDA(cudaMemcpyAsync(host, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
   SV_CUDA(cudaStreamSynchronize(s->stream));
+  if (*host) {
+    SV_CUDA(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s->stream));
+    SV_CUDA(cudaStreamSynchronize(s->stream));
+    return set_error(SV_ETIMEOUT, "a bounded device wait ran out; the last batch is incomplete");
+  }
   return SV_OK;
 }
 
@@ -426,35 +470,6 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
   return launch_dense_gate(s, t, c, U);
 }
 
-static sv_status get_program(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
-                             const CachedProgram **out, uint64_t *key_out, Opts *o_out) {
-  if (!s) return set_error(SV_EINVAL, "null state");
-  if (!c) return set_error(SV_EINVAL, "null circuit");
-  const Opts o = resolve(s, opt, 1);
-  Hasher H;
-  H.val(circuit_hash(c, 0x51));
-  H.val(o.fusion_k);
-  H.val(o.tile_m);
-  H.val(o.L);
-  H.val(o.mode);
-  H.val((int)s->dt);
-  if (params && c->n_params > 0) H.bytes(params, sizeof(double) * c->n_params);
-  const uint64_t key = H.h;
-  auto ck = std::make_pair((const sv_state *)s, key);
-  auto it = g_cache.find(ck);
-  if (it == g_cache.end()) {
-    std::vector<Gate> gates;
-    SV_TRY(circuit_to_gates(c, params, s->n, gates, false));
-    CachedProgram cp;
-    SV_TRY(build_circuit_program(s, gates, o, cp));
-    if (g_cache.size() > 64) g_cache.clear();
-    it = g_cache.emplace(ck, std::move(cp)).first;
-  }
-  *out = &it->second;
-  *key_out = key;
-  *o_out = o;
-  return SV_OK;
-}
 
 sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt) {
   const CachedProgram *cp = nullptr;

@@ -90,6 +90,22 @@ struct TilePass {
   void *v1;               // vector 1 when tbl1 is null
 };
 
+// Arguments of the persistent batch kernel (all pointers are device memory).
+struct PersistArgs {
+  const TilePass *passes;            // ndesc pass descriptors, wave-major order
+  const unsigned long long *first_item;  // first queue item (chunk) of each descriptor
+  const int32_t *dep;                // descriptor this one waits for, or -1
+  const uint32_t *ntiles;            // tiles of each descriptor
+  const uint32_t *chunk;             // tiles per queue item of each descriptor
+  uint32_t *done;                    // finished tiles per descriptor (zeroed before launch)
+  unsigned long long *next_item;     // queue head (zeroed before launch)
+  uint32_t *err;                     // set to 1 when a bounded wait runs out
+  unsigned long long total_items;    // queue items (chunks)
+  uint32_t ndesc;
+  uint32_t pad;
+  uint64_t spin_limit;               // polls per wait
+};
+
 // ---------------------------------------------------------------------------
 // host-side gate representation and planners
 // ---------------------------------------------------------------------------
@@ -172,6 +188,7 @@ struct sv_state {
   char *pinned = nullptr;
   size_t pinned_bytes = 0;
   cudaEvent_t staged = nullptr;     // last upload from `pinned` finished
+  cudaStream_t capture = nullptr;   // library-owned stream used only to record CUDA graphs
   // program cache: key -> program
   std::unordered_map<uint64_t, sv::DeviceProgram> programs;
   uint64_t resident_key = 0;        // program currently in the workspace program area
@@ -192,6 +209,7 @@ size_t amp_bytes(sv_dtype dt);
 int lmin(sv_dtype dt);            // low qubits a tile must keep contiguous (16-byte copies)
 int mmax(sv_dtype dt, int nvec);  // largest tile that fits shared memory
 constexpr size_t kWsScalars = 0;            // FP64 result slots (4 KB)
+constexpr size_t kWsErrFlag = 3072;         // uint32 set by a bounded device wait that ran out
 constexpr size_t kWsGateMat = 64 << 10;     // single-gate matrix scratch (k >= 4)
 
 // program building / upload / launch (sv_api.cu)
@@ -209,6 +227,8 @@ struct ProgLayout {
 ProgLayout layout_of(const DeviceProgram &p, size_t tbl_bytes, size_t pmats_bytes);
 sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, size_t>> &parts,
                        const std::vector<size_t> &offs, size_t total);
+sv_status stage_upload_to(sv_state *s, void *dst, const std::vector<std::pair<const void *, size_t>> &parts,
+                          const std::vector<size_t> &offs, size_t total);
 struct LaunchEnv {
   int batch = 1;
   void *const *tbl0 = nullptr;
@@ -225,6 +245,20 @@ struct Opts {
   int fusion_k, tile_m, L, prec, mode;
 };
 Opts resolve(const sv_state *s, const sv_options *o, int nvec);
+// Fill fusion_k / tile_m that the caller left at 0 from the autotuner's
+// cache for this circuit's shape (sv_batch.cu).
+void tuned_options(const sv_state *s, const sv_circuit *c, const sv_options *opt, Opts &o);
+// Cached plain-circuit program (one vector) and its lookup.
+struct CachedProgram {
+  DeviceProgram prog;
+  std::vector<uint32_t> op0s;
+  ProgLayout lay;
+  std::vector<Block> blocks;   // for per-gate mode
+};
+sv_status get_program(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
+                      const CachedProgram **out, uint64_t *key_out, Opts *o_out);
+sv_status upload_program(sv_state *s, const CachedProgram &cp, uint64_t key);
+void drop_graphs(const sv_state *s);
 uint64_t circuit_hash(const sv_circuit *c, uint64_t salt);
 
 // kernels (launchers), all enqueue on s->stream
@@ -244,6 +278,9 @@ sv_status launch_sample_shots(sv_state *s, int64_t shot0, int64_t count, uint64_
 size_t sample_shot_offset(int n);
 int64_t sample_shot_capacity();
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch);
+sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream);
+sv_status launch_tile_persist(sv_state *s, const PersistArgs &A, int m_max, int *grid_out, cudaStream_t st);
+sv_status launch_wait_selftest(cudaStream_t st, const uint32_t *never, uint32_t *err, uint64_t limit);
 int tile_threads(int m, sv_dtype dt);
 size_t tile_smem(sv_dtype dt, int m, int nvec);
 

@@ -1,0 +1,130 @@
+"""Batched execution of uneven circuits in one persistent launch (plain and
+CUDA-graph replay), the autotuner, and the bounded device wait."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from conftest import fidelity_metrics
+
+pytestmark = pytest.mark.gpu
+
+
+def batch_apply(svlib, states, circs, opts=None, params=None):
+    from paper_2106_13995_gb300 import _native as N
+    ms = [svlib.marshal(c) for c in circs]
+    B = len(states)
+    hs = (C.c_void_p * B)(*[s.h.value for s in states])
+    cs = (C.POINTER(N.SvCircuit) * B)(*[C.pointer(m.c) for m in ms])
+    N.check(N.lib().sv_apply_circuit_batch(hs, B, cs, None, C.byref(opts) if opts else None))
+    N.check(N.lib().sv_synchronize(states[0].h))
+    return ms
+
+
+def small_uneven(count, nmin, nmax, depth, seed):
+    return W.uneven_batch(count=count, nmin=nmin, nmax=nmax, depth=depth, seed=seed)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_persistent_batch_matches_per_circuit_and_oracle(svlib, oracle, dt):
+    circs = small_uneven(24, 6, 18, 8, seed=7)
+    states = [svlib.StateVector(c.n_qubits, dt).set_basis(0) for c in circs]
+    batch_apply(svlib, states, circs)
+    for c, s in zip(circs, states):
+        got = s.numpy()
+        ref = svlib.StateVector(c.n_qubits, dt).set_basis(0).apply_circuit(c).numpy()
+        assert np.array_equal(got, ref), c.name          # same programs, same arithmetic
+        inf, _ = fidelity_metrics(oracle.run(c), got)
+        assert inf <= (1e-5 if dt == "c64" else 1e-12), (c.name, inf)
+
+
+def test_graph_replay(svlib):
+    from paper_2106_13995_gb300 import _native as N
+    circs = small_uneven(12, 8, 20, 6, seed=3)
+    states = [svlib.StateVector(c.n_qubits, "c64") for c in circs]
+    opts = svlib.options(mode=N.SV_MODE_TILED_GRAPH)
+    outs = []
+    for rep in range(3):
+        for s in states:
+            s.set_basis(0)
+        batch_apply(svlib, states, circs, opts)
+        outs.append([s.numpy() for s in states])
+    for rep in (1, 2):
+        for a, b in zip(outs[0], outs[rep]):
+            assert np.array_equal(a, b)
+    for c, s, got in zip(circs, states, outs[0]):
+        ref = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c).numpy()
+        assert np.array_equal(got, ref)
+
+
+def test_uneven_256_full_size(svlib, oracle):
+    """256 circuits, widths 10..24, depth 40, one persistent launch; every
+    state equals its per-circuit run; a seeded subset is checked against the
+    FP64 oracle (all widths <= 14 and two wider circuits)."""
+    circs = W.uneven_batch()
+    states = [svlib.StateVector(c.n_qubits, "c64").set_basis(0) for c in circs]
+    batch_apply(svlib, states, circs)
+    rng = np.random.default_rng(0)
+    wide = [i for i, c in enumerate(circs) if c.n_qubits >= 20]
+    check = [i for i, c in enumerate(circs) if c.n_qubits <= 14][:24] + list(rng.choice(wide, 2, replace=False))
+    worst = 0.0
+    for i in range(len(circs)):
+        c, s = circs[i], states[i]
+        if c.n_qubits <= 16 or i in check:
+            got = s.numpy()
+            ref = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c).numpy()
+            assert np.array_equal(got, ref), c.name
+            if i in check:
+                inf, _ = fidelity_metrics(oracle.run(c), got)
+                worst = max(worst, inf)
+                assert inf <= 1e-5, (c.name, inf)
+        s.close()
+    print(f"uneven batch: worst 1-F {worst:.2e}")
+
+
+def test_autotune_then_use(svlib, oracle):
+    c = W.random_u3_cz(16, 10, 5)
+    scratch = svlib.StateVector(16, "c64")
+    from paper_2106_13995_gb300 import _native as N
+    o = svlib.options()
+    N.check(N.lib().sv_autotune(scratch.h, svlib.marshal(c).ref(), C.byref(o)))
+    assert 2 <= o.fusion_k <= 6 and 10 <= o.tile_m <= 16
+    s = svlib.StateVector(16, "c64").set_basis(0).apply_circuit(c)    # uses the tuned choice
+    inf, _ = fidelity_metrics(oracle.run(c), s.numpy())
+    assert inf <= 1e-5
+
+
+def test_bounded_wait_times_out_and_context_survives(svlib):
+    from paper_2106_13995_gb300 import _native as N
+    st = torch.cuda.current_stream()
+    rc = N.lib().sv_wait_selftest(C.c_void_p(st.cuda_stream), 2000)
+    assert rc == N.SV_ETIMEOUT
+    assert b"ran out" in N.lib().sv_last_error()
+    # the context is still usable
+    s = svlib.StateVector(10, "c64").set_basis(3)
+    assert s.numpy()[3] == 1
+
+
+def test_batch_timeout_reports_status(svlib):
+    """A one-poll budget makes dependent waits run out; the launch stops and
+    sv_synchronize reports SV_ETIMEOUT (or SV_OK if every wait happened to be
+    satisfied at the first poll); afterwards the states work normally."""
+    from paper_2106_13995_gb300 import _native as N
+    circs = [W.random_u3_cz(22, 6, 1), W.random_u3_cz(21, 6, 2)]
+    states = [svlib.StateVector(c.n_qubits, "c64").set_basis(0) for c in circs]
+    ms = [svlib.marshal(c) for c in circs]
+    hs = (C.c_void_p * 2)(*[s.h.value for s in states])
+    cs = (C.POINTER(N.SvCircuit) * 2)(*[C.pointer(m.c) for m in ms])
+    o = svlib.options(timeout_cycles=1)
+    N.check(N.lib().sv_apply_circuit_batch(hs, 2, cs, None, C.byref(o)))
+    rc = N.lib().sv_synchronize(states[0].h)
+    assert rc in (N.SV_OK, N.SV_ETIMEOUT)
+    assert N.lib().sv_synchronize(states[0].h) == N.SV_OK       # flag cleared
+    for c, s in zip(circs, states):
+        s.set_basis(0)
+    batch_apply(svlib, states, circs)
+    for c, s in zip(circs, states):
+        ref = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c).numpy()
+        assert np.array_equal(s.numpy(), ref)
