@@ -1,0 +1,335 @@
+// K7: fused 5-qubit dense block on the tensor cores (tcgen05, TMEM).
+//
+// A k-qubit block U acts on 2^{n-k} groups of 2^k amplitudes; with the
+// amplitudes of group g interleaved as a real row x_g = (re_0, im_0, re_1, ...)
+// the update is x_g <- x_g R^T with the real embedding
+//   R[2r][2c] = Re U[r][c],  R[2r][2c+1] = -Im U[r][c],
+//   R[2r+1][2c] = Im U[r][c], R[2r+1][2c+1] = Re U[r][c],
+// a dense (2^{n-k} x 2^{k+1}) x (2^{k+1} x 2^{k+1}) real GEMM -- the only
+// step of the method that is a real contraction, so it goes to the tensor
+// cores.  For k = 5 each CTA takes 128 groups (M = 128, N = K = 64).
+//
+// Precision: FP32 inputs are split x = x_hi + x_lo (TF32 or BF16 parts) and
+// the three products hi*hi + hi*lo + lo*hi are accumulated in FP32 in TMEM.
+//
+// Per tile: every thread gathers one group's 32 amplitudes from HBM, writes
+// the hi/lo rows into shared memory in the canonical no-swizzle K-major
+// layout (core matrices of 8 rows x 16 bytes), one thread issues the MMAs
+// and commits them to an mbarrier, every warp reads its 32 TMEM lanes back
+// and scatters the new amplitudes.  All waits are bounded; on timeout the
+// CTA raises the error flag, waits (bounded) for its own MMAs, frees its TMEM
+// and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "sv_device.cuh"
+#include "sv_internal.h"
+
+namespace sv {
+
+constexpr int kTcK = 5;              // qubits per block
+constexpr int kTcRows = 128;         // groups per tile (MMA M)
+constexpr int kTcCols = 64;          // 2^{k+1} real columns (MMA N and K)
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTmemCols = 64;
+
+struct TcArgs {
+  float2 *amps;
+  uint64_t ngroups;          // 2^{n-5}
+  uint64_t tmask;            // target bits
+  uint64_t off[32];          // index offset of local basis state y
+  const uint32_t *bmat;      // device: B_hi then B_lo, each 64 x 64 words in core-matrix layout
+  uint32_t *err;             // error flag (set on a timed-out wait)
+  uint32_t mode;             // 1 = TF32 x3, 2 = BF16 x3
+  uint32_t spin_limit;       // mbarrier polls per wait
+};
+
+// shared-memory layout (bytes)
+constexpr uint32_t kABytes = kTcRows * kTcCols * 4;   // one fp32 operand copy (32 KB)
+constexpr uint32_t kBBytes = kTcCols * kTcCols * 4;   // 16 KB
+constexpr uint32_t kSmA = 0;                          // A_hi, A_lo
+constexpr uint32_t kSmB = 2 * kABytes;                // B_hi, B_lo
+constexpr uint32_t kSmBar = kSmB + 2 * kBBytes;       // mbarrier (8 B) + TMEM address (4 B)
+constexpr uint32_t kSmTotal = kSmBar + 16;
+
+// Canonical K-major, no swizzle: element (row, k) of a [rows x K] operand of
+// 4-byte elements sits in core matrix (row / 8, k / 4) at byte
+// (k / 4) * (rows * 16) + (row / 8) * 128 + (row % 8) * 16 + (k % 4) * 4.
+// The leading-dimension offset (next core matrix along K) is rows * 16, the
+// stride offset (next 8 rows) is 128.  For 2-byte elements the same layout
+// holds with 8 elements per 16 bytes.
+__host__ __device__ constexpr uint32_t cm_offset(uint32_t row, uint32_t chunk16, uint32_t rows) {
+  return chunk16 * (rows * 16) + (row / 8) * 128 + (row % 8) * 16;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;            // descriptor version for this architecture
+  // base offset 0, LBO mode 0, layout type 0 (no swizzle)
+  return d;
+}
+
+// instruction descriptor: FP32 accumulate, A/B format (TF32 = 2, BF16 = 1),
+// both K-major, N = 64, M = 128
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTcCols >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate, uint32_t mode) {
+  if (mode == 1)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; i++) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// 64 consecutive TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// TF32 part: FP32 bits with the low 13 mantissa bits cleared (exact split)
+__device__ __forceinline__ uint32_t tf32_hi(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(const __grid_constant__ TcArgs A) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t bar = sbase + kSmBar;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kSmBar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  const uint32_t elem = A.mode == 1 ? 4 : 2;
+  const uint32_t a_bytes = kTcRows * kTcCols * elem, b_bytes = kTcCols * kTcCols * elem;
+  // B operand (hi and lo parts, 2 * b_bytes) into shared memory, once per CTA
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.bmat);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm + kSmB);
+    for (uint32_t i = tid; i < 2 * b_bytes / 16; i += kTcThreads) dst[i] = src[i];
+  }
+  __shared__ uint32_t s_ok;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = instr_desc(A.mode == 1 ? 2u : 1u);
+  const uint32_t a_lbo = kTcRows * 16, b_lbo = kTcCols * 16;   // bytes between K core matrices
+  // bytes of K per MMA instruction: 8 TF32 or 16 BF16 = 32 bytes = 2 core matrices
+  const uint32_t ksteps = A.mode == 1 ? kTcCols / 8 : kTcCols / 16;
+
+  uint32_t phase = 0;
+  bool failed = false;
+  const uint64_t ntiles = A.ngroups / kTcRows;
+  for (uint64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    // gather this thread's group and write its hi/lo row
+    const uint64_t g = tile * kTcRows + tid;
+    const uint64_t base = ins0_mask64(g, A.tmask);
+    float2 x[32];
+#pragma unroll
+    for (int y = 0; y < 32; y++) x[y] = __ldcs(A.amps + base + A.off[y]);
+    if (A.mode == 1) {
+#pragma unroll
+      for (int c = 0; c < 16; c++) {   // 16-byte chunk c = columns 4c .. 4c+3 = amplitudes 2c, 2c+1
+        const float f[4] = {x[2 * c].x, x[2 * c].y, x[2 * c + 1].x, x[2 * c + 1].y};
+        uint4 hi, lo;
+        hi.x = tf32_hi(f[0]); hi.y = tf32_hi(f[1]); hi.z = tf32_hi(f[2]); hi.w = tf32_hi(f[3]);
+        lo.x = __float_as_uint(f[0] - __uint_as_float(hi.x));
+        lo.y = __float_as_uint(f[1] - __uint_as_float(hi.y));
+        lo.z = __float_as_uint(f[2] - __uint_as_float(hi.z));
+        lo.w = __float_as_uint(f[3] - __uint_as_float(hi.w));
+        const uint32_t o = cm_offset(tid, c, kTcRows);
+        *reinterpret_cast<uint4 *>(sm + kSmA + o) = hi;
+        *reinterpret_cast<uint4 *>(sm + kSmA + a_bytes + o) = lo;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; c++) {    // 16-byte chunk c = 8 BF16 columns = amplitudes 4c .. 4c+3
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const float2 a = x[4 * c + e];
+          const __nv_bfloat16 hr = __float2bfloat16_rn(a.x), hi_ = __float2bfloat16_rn(a.y);
+          const __nv_bfloat16 lr = __float2bfloat16_rn(a.x - __bfloat162float(hr));
+          const __nv_bfloat16 li = __float2bfloat16_rn(a.y - __bfloat162float(hi_));
+          hw[e] = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi_) << 16);
+          lw[e] = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
+        }
+        const uint32_t o = cm_offset(tid, c, kTcRows);
+        *reinterpret_cast<uint4 *>(sm + kSmA + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(sm + kSmA + a_bytes + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+      const uint32_t a_hi = sbase + kSmA, a_lo = a_hi + a_bytes;
+      const uint32_t b_hi = sbase + kSmB, b_lo = b_hi + b_bytes;
+      // D = A_hi B_hi + A_hi B_lo + A_lo B_hi
+      const uint32_t as[3] = {a_hi, a_hi, a_lo}, bs[3] = {b_hi, b_lo, b_hi};
+      for (int t = 0; t < 3; t++)
+        for (uint32_t s = 0; s < ksteps; s++) {
+          const uint64_t ad = smem_desc(as[t] + s * 2 * a_lbo, a_lbo, 128);
+          const uint64_t bd = smem_desc(bs[t] + s * 2 * b_lbo, b_lbo, 128);
+          mma_issue(tmem, ad, bd, idesc, (t > 0 || s > 0) ? 1u : 0u, A.mode);
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                   : "memory");
+    }
+    // thread 0 waits (bounded) and tells the others, so all take one branch
+    if (tid == 0) {
+      s_ok = mbar_wait(bar, phase, A.spin_limit) ? 1u : 0u;
+      if (!s_ok) {
+        atomicExch(A.err, 1u);
+        mbar_wait(bar, phase, A.spin_limit);   // give the MMAs a last bounded chance to drain
+      }
+    }
+    __syncthreads();
+    if (!s_ok) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    uint32_t r[64];
+    tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16), r);
+#pragma unroll
+    for (int y = 0; y < 32; y++) __stcs(A.amps + base + A.off[y], make_float2(__uint_as_float(r[2 * y]),
+                                                                             __uint_as_float(r[2 * y + 1])));
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();   // TMEM and shared rows are free for the next tile
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// Host: real embedding R of U (64 x 64), split into hi/lo parts and laid out
+// as the K-major B operand (B[n][k] = R[n][k]).
+static void build_b(const std::vector<cd> &U, uint32_t mode, std::vector<uint32_t> &out) {
+  const int D = 32, N = 64;
+  std::vector<float> R((size_t)N * N);
+  for (int r = 0; r < D; r++)
+    for (int c = 0; c < D; c++) {
+      const float ur = (float)U[(size_t)r * D + c].real(), ui = (float)U[(size_t)r * D + c].imag();
+      R[(size_t)(2 * r) * N + 2 * c] = ur;
+      R[(size_t)(2 * r) * N + 2 * c + 1] = -ui;
+      R[(size_t)(2 * r + 1) * N + 2 * c] = ui;
+      R[(size_t)(2 * r + 1) * N + 2 * c + 1] = ur;
+    }
+  const size_t words = (size_t)N * N * (mode == 1 ? 1 : 2) / 2;   // per part, in 32-bit words
+  out.assign(2 * (mode == 1 ? (size_t)N * N : (size_t)N * N / 2), 0u);
+  unsigned char *hi = reinterpret_cast<unsigned char *>(out.data());
+  unsigned char *lo = hi + (mode == 1 ? (size_t)N * N * 4 : (size_t)N * N * 2);
+  (void)words;
+  for (int n = 0; n < N; n++)
+    for (int k = 0; k < N; k++) {
+      const float v = R[(size_t)n * N + k];
+      if (mode == 1) {
+        uint32_t bits;
+        std::memcpy(&bits, &v, 4);
+        const uint32_t h = bits & 0xFFFFE000u;
+        float hf;
+        std::memcpy(&hf, &h, 4);
+        const float l = v - hf;
+        const uint32_t o = cm_offset(n, k / 4, N) + (k % 4) * 4;
+        std::memcpy(hi + o, &h, 4);
+        std::memcpy(lo + o, &l, 4);
+      } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        const uint32_t o = cm_offset(n, k / 8, N) + (k % 8) * 2;
+        std::memcpy(hi + o, &h, 2);
+        std::memcpy(lo + o, &l, 2);
+      }
+    }
+}
+
+size_t tc_matrix_words(sv_prec mode) { return mode == SV_PREC_TC_TF32X3 ? 2 * 64 * 64 : 64 * 64; }
+
+void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t> &out) {
+  build_b(U, mode == SV_PREC_TC_TF32X3 ? 1u : 2u, out);
+}
+
+sv_status launch_dense_tc(sv_state *s, void *amps, const int *targets, const uint32_t *bmat_dev, sv_prec mode,
+                          uint64_t spin_limit, cudaStream_t stream) {
+  if (s->dt != SV_C64) return set_error(SV_EUNSUPPORTED, "tensor-core blocks need a complex64 state");
+  if (s->n < kTcK + 7) return set_error(SV_EUNSUPPORTED, "tensor-core blocks need at least 12 qubits");
+  if (((uintptr_t)bmat_dev) & 15) return set_error(SV_EINVAL, "internal: tensor-core operand misaligned");
+  TcArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.amps = reinterpret_cast<float2 *>(amps);
+  A.ngroups = 1ull << (s->n - kTcK);
+  for (int y = 0; y < 32; y++) {
+    uint64_t o = 0;
+    for (int j = 0; j < kTcK; j++) o |= (uint64_t)((y >> j) & 1) << targets[j];
+    A.off[y] = o;
+  }
+  A.tmask = A.off[31];
+  A.bmat = bmat_dev;
+  A.err = reinterpret_cast<uint32_t *>(s->ws + kWsCtrl + kWsErrFlag);
+  A.mode = mode == SV_PREC_TC_TF32X3 ? 1u : 2u;
+  A.spin_limit = (uint32_t)std::min<uint64_t>(spin_limit ? spin_limit : (1u << 22), 0xFFFFFFFFu);
+  static bool attr = false;
+  if (!attr) {
+    SV_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal));
+    attr = true;
+  }
+  const uint64_t ntiles = A.ngroups / kTcRows;
+  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)s->sm_count * 2);
+  k_dense_tc<<<grid, kTcThreads, kSmTotal, stream>>>(A);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+}  // namespace sv

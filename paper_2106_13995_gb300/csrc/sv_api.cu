@@ -42,7 +42,7 @@ size_t red_bytes(int n) {
 // ---------------------------------------------------------------------------
 Opts resolve(const sv_state *s, const sv_options *o, int nvec) {
   Opts r;
-  r.fusion_k = (o && o->fusion_k > 0) ? o->fusion_k : 3;
+  r.fusion_k = (o && o->fusion_k > 0) ? o->fusion_k : (o && o->prec != SV_PREC_PLAIN ? 5 : 3);
   r.tile_m = (o && o->tile_m > 0) ? o->tile_m : (s->dt == SV_C64 ? 12 : 12) - (nvec - 1);
   r.L = s->dt == SV_C64 ? 4 : 3;
   r.prec = o ? o->prec : SV_PREC_PLAIN;
@@ -213,6 +213,14 @@ sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, si
   return SV_OK;
 }
 
+sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream_t st) {
+  if (!(tp.flags & kPassTC)) return launch_tile_pass_on(s, tp, batch, st);
+  int t[5];
+  for (int j = 0; j < 5; j++) t[j] = tp.hi_pos[j];
+  const uint32_t *b = reinterpret_cast<const uint32_t *>(static_cast<const char *>(tp.mats) + 16 * (size_t)tp.mat0);
+  return launch_dense_tc(s, tp.v0, t, b, (sv_prec)((tp.flags >> 9) & 3), 0, st);
+}
+
 // Launch every pass of a program.
 sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &L,
                                 const std::vector<uint32_t> &op0s, const LaunchEnv &E) {
@@ -230,7 +238,7 @@ sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &
     tp.tbl1 = E.tbl1;
     tp.v0 = E.v0;
     tp.v1 = E.v1;
-    SV_TRY(launch_tile_pass(s, tp, E.batch));
+    SV_TRY(launch_any_pass(s, tp, E.batch, s->stream));
   }
   return SV_OK;
 }
@@ -244,10 +252,43 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
   int m = o.tile_m, L = o.L;
   if (!fit_tile(out.blocks, s->n, lmin(s->dt), mmax(s->dt, 1), m, L))
     return set_error(SV_EUNSUPPORTED, "a fused block does not fit a shared-memory tile");
-  std::vector<PassPlan> passes = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, kMaxMatPerPass);
-  if (passes.empty() && !out.blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
   BuildCtx b{s->dt, s->n, m, L, 1, 0};
-  for (const PassPlan &P : passes) SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
+  // With a tensor-core precision mode, dense 5-qubit blocks become their own
+  // passes; the blocks between them are planned into tile passes as usual.
+  const bool tc = o.prec != SV_PREC_PLAIN && s->dt == SV_C64 && s->n >= 12;
+  std::vector<Block> seg;
+  auto flush = [&]() -> sv_status {
+    if (seg.empty()) return SV_OK;
+    std::vector<PassPlan> passes = plan_passes(seg, s->n, m, L, kMaxOpsPerPass, kMaxMatPerPass);
+    if (passes.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
+    for (const PassPlan &P : passes) SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
+    seg.clear();
+    return SV_OK;
+  };
+  for (const Block &blk : out.blocks) {
+    const bool is_tc = tc && blk.kind == TOP_DENSE && blk.qubits.size() == 5 && blk.controls.empty() && !blk.diag;
+    if (!is_tc) {
+      seg.push_back(blk);
+      continue;
+    }
+    SV_TRY(flush());
+    TilePass tp;
+    std::memset(&tp, 0, sizeof(tp));
+    tp.n = s->n;
+    tp.m = s->n;
+    tp.nvec = 1;
+    tp.flags = kPassTC | ((uint32_t)o.prec << 9);
+    for (int j = 0; j < 5; j++) tp.hi_pos[j] = (int8_t)blk.qubits[j];
+    while (out.prog.mats.size() % 16) out.prog.mats.push_back(0);
+    tp.mat0 = (uint32_t)(out.prog.mats.size() / 16);
+    std::vector<uint32_t> packed;
+    tc_pack_matrix(blk.U, (sv_prec)o.prec, packed);
+    const uint8_t *pb = reinterpret_cast<const uint8_t *>(packed.data());
+    out.prog.mats.insert(out.prog.mats.end(), pb, pb + packed.size() * 4);
+    out.op0s.push_back((uint32_t)out.prog.ops.size());
+    out.prog.passes.push_back(tp);
+  }
+  SV_TRY(flush());
   out.lay = layout_of(out.prog, 0, 0);
   return SV_OK;
 }
@@ -291,6 +332,7 @@ sv_status get_program(sv_state *s, const sv_circuit *c, const double *params, co
   H.val(o.tile_m);
   H.val(o.L);
   H.val(o.mode);
+  H.val(o.prec);
   H.val((int)s->dt);
   if (params && c->n_params > 0) H.bytes(params, sizeof(double) * c->n_params);
   const uint64_t key = H.h;

@@ -68,6 +68,10 @@ static_assert(sizeof(TileOp) == 32, "TileOp must stay 32 bytes");
 // Per-pass launch description (passed by value as a kernel parameter).
 constexpr int kMaxQ = 34;
 constexpr uint8_t kGenBatchMat = 0x80;   // TileOp.gen flag: matrix from the per-batch pool
+// TilePass.flags: this entry is not a tile pass but one 5-qubit dense block on
+// the tensor cores; hi_pos[0..4] hold its targets, mat0 the 16-byte index of
+// its packed operand in the matrix pool, bits 9..10 the sv_prec mode.
+constexpr uint32_t kPassTC = 0x100;
 struct TilePass {
   int32_t n;              // state qubits
   int32_t m;              // tile qubits
@@ -77,6 +81,8 @@ struct TilePass {
   int8_t out_pos[kMaxQ];  // sorted global positions not in the tile (n - m of them)
   uint32_t flags;         // bit0: v1 is zeroed by the pass, do not load it
   uint32_t nvec;          // 1 or 2 vectors per tile
+  uint32_t mat0;          // tensor-core entries (kPassTC): 16-byte index of the operand in the pool
+  uint32_t pad0;
   const TileOp *ops;      // device: this pass's ops
   const void *mats;       // device: shared matrix pool
   const void *pmats;      // device: per-batch matrix pool
@@ -279,6 +285,13 @@ size_t sample_shot_offset(int n);
 int64_t sample_shot_capacity();
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch);
 sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream);
+// tensor-core 5-qubit block (k_tc.cu)
+size_t tc_matrix_words(sv_prec mode);
+void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t> &out);
+sv_status launch_dense_tc(sv_state *s, void *amps, const int *targets, const uint32_t *bmat_dev, sv_prec mode,
+                          uint64_t spin_limit, cudaStream_t stream);
+// one pass of a program (tile pass or tensor-core block) on stream st
+sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream_t st);
 sv_status launch_tile_persist(sv_state *s, const PersistArgs &A, int m_max, int *grid_out, cudaStream_t st);
 sv_status launch_wait_selftest(cudaStream_t st, const uint32_t *never, uint32_t *err, uint64_t limit);
 int tile_threads(int m, sv_dtype dt);

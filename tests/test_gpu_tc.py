@@ -1,0 +1,76 @@
+"""Fused 5-qubit dense blocks on the tensor cores (tcgen05): split-TF32 and
+split-BF16 (three products, FP32 accumulation) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import fidelity_metrics
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"tf32x3": 2, "bf16x3": 1}
+# per-block error budget of each split mode (relative amplitude error)
+AMP_TOL = {"tf32x3": 2e-6, "bf16x3": 6e-5}
+
+
+def one_block_circuit(n, targets, rng):
+    c = W.Circuit(n)
+    c.ops.append(W.Op("MATRIX", tuple(targets), matrix=W.random_unitary(5, rng)))
+    return c
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("targets", [(0, 1, 2, 3, 4), (4, 3, 2, 1, 0), (7, 2, 11, 0, 13), (13, 12, 11, 10, 9),
+                                     (1, 5, 9, 12, 3)])
+def test_single_block(svlib, oracle, mode, targets):
+    rng = np.random.default_rng(sum(targets))
+    n = 14
+    c = one_block_circuit(n, targets, rng)
+    psi0 = W.random_state(n, rng)
+    cast = psi0.astype(np.complex64).astype(np.complex128)
+    s = svlib.StateVector(n, "c64").load(psi0)
+    opts = svlib.options(prec=MODES[mode])
+    nb, npass = s.plan_info(c, opts=opts)
+    assert nb == 1 and npass == 1
+    s.apply_circuit(c, opts=opts)
+    got = s.numpy().astype(np.complex128)
+    want = oracle.run(c, cast)
+    inf, amp = fidelity_metrics(want, got)
+    scale = np.max(np.abs(want))
+    assert amp <= AMP_TOL[mode] * scale, (amp, scale)
+    assert inf <= 1e-8
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_large_state_tiles(svlib, oracle, mode):
+    """Many 128-group tiles per CTA (grid-stride loop), 20 qubits."""
+    rng = np.random.default_rng(5)
+    n = 20
+    c = one_block_circuit(n, (19, 3, 0, 10, 17), rng)
+    psi0 = W.random_state(n, rng)
+    s = svlib.StateVector(n, "c64").load(psi0)
+    s.apply_circuit(c, opts=svlib.options(prec=MODES[mode]))
+    want = oracle.run(c, psi0.astype(np.complex64).astype(np.complex128))
+    inf, amp = fidelity_metrics(want, s.numpy())
+    assert inf <= 1e-8 and amp <= AMP_TOL[mode] * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_circuits_with_fused_5q_blocks(svlib, oracle, mode):
+    for c in (W.random_u3_cz(16, 12, 3), W.grid_random(4, 4, 10, 2),
+              W.remove_qubits(W.grid_random(5, 6, 8, 1), 10, 3)):
+        opts = svlib.options(prec=MODES[mode])
+        s = svlib.StateVector(c.n_qubits, "c64").set_basis(0)
+        nb, npass = s.plan_info(c, opts=opts)
+        s.apply_circuit(c, opts=opts)
+        inf, amp = fidelity_metrics(oracle.run(c), s.numpy())
+        assert inf <= 1e-5, (c.name, mode, inf)
+        print(f"{c.name} {mode}: blocks {nb}, passes {npass}, 1-F {inf:.2e}, max|d| {amp:.2e}")
+
+
+def test_tc_rejected_for_complex128(svlib, oracle):
+    """complex128 states keep FP64 CUDA-core arithmetic in every mode."""
+    c = W.random_u3_cz(13, 4, 1)
+    s = svlib.StateVector(13, "c128").set_basis(0).apply_circuit(c, opts=svlib.options(prec=2))
+    inf, _ = fidelity_metrics(oracle.run(c), s.numpy())
+    assert inf <= 1e-12
