@@ -59,8 +59,11 @@ typedef enum {
 
 typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
 
-/* Arithmetic used for dense fused blocks of 4..6 qubits (complex64 states
- * only; complex128 states always use FP64 CUDA-core arithmetic). */
+/* Arithmetic of fused dense blocks.  In the tensor-core modes the fusion
+ * width defaults to 5 and every dense 5-qubit block is applied on the tensor
+ * cores (complex64 states of >= 12 qubits): as a pass of its own by default,
+ * or inside 12-qubit tile passes when sv_options.tile_m is set to 12.
+ * complex128 states always use FP64 CUDA-core arithmetic. */
 typedef enum {
   SV_PREC_PLAIN = 0,       /* FP32 FMA on CUDA cores */
   SV_PREC_TC_BF16X3 = 1,   /* tensor cores, split-BF16 (3 products), FP32 accumulate */

@@ -17,6 +17,10 @@
 // those strides land on a few banks (up to 8-way conflicts for three low
 // targets), with it every access pattern of the op list spreads over all
 // banks.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "sv_device.cuh"
 #include "sv_internal.h"
 
@@ -180,6 +184,124 @@ __device__ void grad_op(const typename Cx<R>::T *__restrict__ psi,
   block_acc<R>(part, acc + op.slot);
 }
 
+// ---- TOP_TC: 5-qubit block on the tensor cores inside a 12-qubit tile -----
+// The tile's 128 groups of 32 amplitudes form the A operand (hi/lo parts of
+// every real column, canonical K-major layout), the packed real embedding of
+// U is the B operand (staged from global memory per op), D (128 x 64 FP32)
+// lives in TMEM.  See k_tc.cu for the operand formats.
+struct TcShared {
+  uint32_t a;        // shared address of A_hi (A_lo follows)
+  uint32_t b;        // shared address of B_hi (B_lo follows)
+  uint32_t bar;      // mbarrier
+  uint32_t tmem;     // TMEM base address
+  uint32_t mode;     // 1 = TF32 x3, 2 = BF16 x3
+  uint32_t *ok;      // shared flag: the MMAs completed
+};
+
+__device__ __forceinline__ uint32_t tf32_part(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
+
+// returns false if the MMA wait ran out (error flag raised)
+__device__ __noinline__ bool tc_op(float2 *__restrict__ v, const TileOp &op, const uint4 *__restrict__ bglob,
+                                   const TcShared &T, uint32_t &phase, uint32_t *err, unsigned char *smem) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const uint32_t elem = T.mode == 1 ? 4 : 2;
+  const uint32_t a_bytes = 128 * 64 * elem, b_bytes = 64 * 64 * elem;
+  unsigned char *sm_a = smem + (T.a - smem_u32(smem));
+  unsigned char *sm_b = smem + (T.b - smem_u32(smem));
+  // B operand
+  for (uint32_t i = tid; i < 2 * b_bytes / 16; i += nthr) reinterpret_cast<uint4 *>(sm_b)[i] = __ldg(bglob + i);
+  uint32_t offs[32], tmask = 0;
+#pragma unroll
+  for (int y = 0; y < 32; y++) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) o |= (uint32_t)((y >> j) & 1) << op.t[j];
+    offs[y] = o;
+  }
+  tmask = offs[31];
+  // A operand: item = (row, quarter of its 32 amplitudes)
+  for (int item = tid; item < 512; item += nthr) {
+    const uint32_t row = item >> 2, q = item & 3;
+    const uint32_t i0 = ins0_mask(row, tmask);
+    float2 x[8];
+#pragma unroll
+    for (int e = 0; e < 8; e++) x[e] = v[sw<float>(i0 + offs[8 * q + e])];
+    if (T.mode == 1) {
+#pragma unroll
+      for (int c = 0; c < 4; c++) {          // 16-byte chunk (4q + c): amplitudes 8q + 2c, +1
+        const float f[4] = {x[2 * c].x, x[2 * c].y, x[2 * c + 1].x, x[2 * c + 1].y};
+        uint4 hi, lo;
+        hi.x = tf32_part(f[0]); hi.y = tf32_part(f[1]); hi.z = tf32_part(f[2]); hi.w = tf32_part(f[3]);
+        lo.x = __float_as_uint(f[0] - __uint_as_float(hi.x));
+        lo.y = __float_as_uint(f[1] - __uint_as_float(hi.y));
+        lo.z = __float_as_uint(f[2] - __uint_as_float(hi.z));
+        lo.w = __float_as_uint(f[3] - __uint_as_float(hi.w));
+        const uint32_t o = cm_offset(row, 4 * q + c, 128);
+        *reinterpret_cast<uint4 *>(sm_a + o) = hi;
+        *reinterpret_cast<uint4 *>(sm_a + a_bytes + o) = lo;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 2; c++) {          // 16-byte chunk (2q + c): amplitudes 8q + 4c .. +3
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const float2 a = x[4 * c + e];
+          const __nv_bfloat16 hr = __float2bfloat16_rn(a.x), hi_ = __float2bfloat16_rn(a.y);
+          const __nv_bfloat16 lr = __float2bfloat16_rn(a.x - __bfloat162float(hr));
+          const __nv_bfloat16 li = __float2bfloat16_rn(a.y - __bfloat162float(hi_));
+          hw[e] = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi_) << 16);
+          lw[e] = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
+        }
+        const uint32_t o = cm_offset(row, 2 * q + c, 128);
+        *reinterpret_cast<uint4 *>(sm_a + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(sm_a + a_bytes + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+    }
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) {
+    const uint32_t idesc = instr_desc(T.mode == 1 ? 2u : 1u);
+    const uint32_t ksteps = T.mode == 1 ? 8 : 4;
+    const uint32_t a_lbo = 128 * 16, b_lbo = 64 * 16;
+    const uint32_t as[3] = {T.a, T.a, T.a + a_bytes}, bs[3] = {T.b, T.b + b_bytes, T.b};
+    for (int t = 0; t < 3; t++)
+      for (uint32_t k = 0; k < ksteps; k++)
+        mma_issue(T.tmem, smem_desc(as[t] + k * 2 * a_lbo, a_lbo, 128), smem_desc(bs[t] + k * 2 * b_lbo, b_lbo, 128),
+                  idesc, (t > 0 || k > 0) ? 1u : 0u, T.mode);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(T.bar)
+                 : "memory");
+    const bool ok = mbar_wait(T.bar, phase, 1u << 22);
+    if (!ok) {
+      atomicExch(err, 1u);
+      mbar_wait(T.bar, phase, 1u << 22);
+    }
+    *T.ok = ok ? 1u : 0u;
+  }
+  __syncthreads();
+  phase ^= 1u;
+  if (!*T.ok) return false;
+  tc_fence_after();
+  // epilogue: warp w reads lanes 32 (w % 4) .. +31 (rows) and a share of the
+  // 64 columns; 16 columns = 8 amplitudes per read
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  const int lq = warp & 3, cgroups = nwarps >> 2;
+  const uint32_t row = 32 * lq + lane;
+  const uint32_t i0 = ins0_mask(row, tmask);
+  for (int cg = warp >> 2; cg < 4; cg += cgroups) {
+    uint32_t r[16];
+    tmem_ld16(T.tmem + ((uint32_t)(32 * lq) << 16) + 16 * cg, r);
+#pragma unroll
+    for (int e = 0; e < 8; e++)
+      v[sw<float>(i0 + offs[8 * cg + e])] = make_float2(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1]));
+  }
+  tc_fence_before();
+  return true;
+}
+
 // 16-byte unit u of the tile <-> shared memory (swizzled amplitude slots)
 template <typename R> struct Unit;
 template <> struct Unit<float> {
@@ -209,8 +331,15 @@ template <> struct Unit<double> {
 // The work of one CTA on one tile.  COH selects L2-coherent loads and stores
 // (bypassing L1), needed when other CTAs of the same launch wrote the tile
 // earlier (the persistent batch kernel); otherwise streaming hints are used.
-template <typename R, bool COH>
-__device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int b, unsigned char *smem_raw) {
+struct TcState {
+  TcShared T;
+  uint32_t phase;
+  bool failed;
+};
+
+template <typename R, bool COH, bool TC = false>
+__device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int b, unsigned char *smem_raw,
+                                          TcState *tcs = nullptr) {
   using C = typename Cx<R>::T;
   const uint32_t TS = 1u << P.m;
   C *v0 = reinterpret_cast<C *>(smem_raw);
@@ -280,6 +409,14 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
       case TOP_GRAD:
         grad_op<R>(v0, v1, P.m, op, acc);
         break;
+      case TOP_TC:
+        if constexpr (TC && sizeof(R) == 4) {
+          if (!tcs->failed && !tc_op(reinterpret_cast<float2 *>(v0), op,
+                                     reinterpret_cast<const uint4 *>(mats + op.mat), tcs->T, tcs->phase, P.err,
+                                     smem_raw))
+            tcs->failed = true;
+        }
+        break;
       case TOP_PAULI: {
         const uint32_t xm = (uint16_t)op.slot;
         const uint32_t zl = op.lcmask;
@@ -320,6 +457,9 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
     }
   }
   __syncthreads();
+  if constexpr (TC) {
+    if (tcs->failed) return;   // the tile is incomplete: leave HBM as it was
+  }
   const bool store0 = !(P.flags & 2u), store1 = P.nvec > 1 && !(P.flags & 4u);
   for (uint32_t i = 0; i * blockDim.x + threadIdx.x < nunits; i++) {
     const uint32_t l = (i * blockDim.x + threadIdx.x) * UN::APU;
@@ -339,6 +479,48 @@ template <typename R>
 __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_constant__ TilePass P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   tile_body<R, false>(P, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// Tile passes that contain tensor-core ops: each CTA allocates its TMEM
+// columns and mbarrier once and walks over tiles (grid-stride).
+constexpr int kTcTileThreads = 256;
+__global__ void __launch_bounds__(kTcTileThreads, 2) k_tile_tc(const __grid_constant__ TilePass P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t TS = 1u << P.m;
+  const uint32_t mode = (P.flags >> 9) & 3;
+  const uint32_t elem = mode == SV_PREC_TC_TF32X3 ? 4 : 2;
+  TcState st;
+  st.phase = 0;
+  st.failed = false;
+  st.T.mode = mode == SV_PREC_TC_TF32X3 ? 1u : 2u;
+  st.T.a = smem_u32(smem_raw) + (uint32_t)((size_t)P.nvec * TS * sizeof(float2));
+  st.T.b = st.T.a + 2 * 128 * 64 * elem;
+  st.T.bar = st.T.b + 2 * 64 * 64 * elem;
+  uint32_t *slots = reinterpret_cast<uint32_t *>(smem_raw + (st.T.bar + 8 - smem_u32(smem_raw)));
+  st.T.ok = slots + 1;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(st.T.bar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slots)),
+                 "r"(64u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  st.T.tmem = slots[0];
+  const uint64_t ntiles = 1ull << (P.n - P.m);
+  for (uint64_t t = blockIdx.x; t < ntiles && !st.failed; t += gridDim.x) {
+    tile_body<float, false, true>(P, t, 0, smem_raw, &st);
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(st.T.tmem), "r"(64u));
 }
 
 // ---------------------------------------------------------------------------
@@ -433,6 +615,10 @@ int tile_threads(int m, sv_dtype dt) {
 }
 
 size_t tile_smem(sv_dtype dt, int m, int nvec) { return (size_t)nvec * ((size_t)1 << m) * amp_bytes(dt); }
+size_t tc_smem_bytes(sv_prec mode) {
+  const size_t elem = mode == SV_PREC_TC_TF32X3 ? 4 : 2;
+  return 2 * 128 * 64 * elem + 2 * 64 * 64 * elem + 16;
+}
 
 
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
@@ -441,6 +627,24 @@ sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
 
 sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream) {
   static bool attr_set[2][64] = {};
+  if (p.flags & kPassHasTC) {
+    if (s->dt != SV_C64 || p.m != kTcTileM || batch != 1)
+      return set_error(SV_EINVAL, "internal: tensor-core ops need a single complex64 state and 12-qubit tiles");
+    const size_t smem = tile_smem(s->dt, p.m, (int)p.nvec) + tc_smem_bytes((sv_prec)((p.flags >> 9) & 3));
+    static bool attr = false;
+    if (!attr) {
+      SV_CUDA(cudaFuncSetAttribute(k_tile_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+      attr = true;
+    }
+    int per_sm = 0;
+    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_tc, kTcTileThreads, smem));
+    const uint64_t ntiles = 1ull << (p.n - p.m);
+    const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(1, per_sm) * s->sm_count);
+    k_tile_tc<<<grid, kTcTileThreads, smem, stream>>>(p);
+    g_launches++;
+    SV_CUDA(cudaGetLastError());
+    return SV_OK;
+  }
   const size_t smem = tile_smem(s->dt, p.m, (int)p.nvec);
   const int dev = s->device & 63;
   const int di = s->dt == SV_C64 ? 0 : 1;

@@ -49,6 +49,9 @@ Opts resolve(const sv_state *s, const sv_options *o, int nvec) {
   r.mode = o ? o->mode : SV_MODE_TILED;
   r.fusion_k = std::min(r.fusion_k, 6);
   r.tile_m = std::max(1, std::min(r.tile_m, s->n));
+  // tensor-core blocks run inside the tile passes only when the caller asks
+  // for 12-qubit tiles explicitly; by default they are passes of their own
+  r.tc_in_tile = o && o->tile_m == kTcTileM && r.prec != SV_PREC_PLAIN;
   r.L = std::min(r.L, r.tile_m);
   if (s->dt == SV_C64 && r.L < 1) r.L = 1;
   return r;
@@ -144,6 +147,14 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
             b.dt == SV_C64 ? put_c<float>(prog.mats, blk.U[e]) : put_c<double>(prog.mats, blk.U[e]);
         }
       }
+    } else if (op.kind == TOP_TC) {
+      while (prog.mats.size() % 16) prog.mats.push_back(0);
+      op.mat = (uint32_t)(prog.mats.size() / ab);
+      std::vector<uint32_t> packed;
+      tc_pack_matrix(blk.U, (sv_prec)b.prec, packed);
+      const uint8_t *pb = reinterpret_cast<const uint8_t *>(packed.data());
+      prog.mats.insert(prog.mats.end(), pb, pb + packed.size() * 4);
+      tp.flags |= kPassHasTC | ((uint32_t)b.prec << 9);
     } else if (op.kind == TOP_GRAD) {
       op.gen = (uint8_t)blk.gen;
       op.slot = (int16_t)blk.slot;
@@ -238,6 +249,7 @@ sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &
     tp.tbl1 = E.tbl1;
     tp.v0 = E.v0;
     tp.v1 = E.v1;
+    tp.err = reinterpret_cast<uint32_t *>(s->ws + kWsCtrl + kWsErrFlag);
     SV_TRY(launch_any_pass(s, tp, E.batch, s->stream));
   }
   return SV_OK;
@@ -252,10 +264,20 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
   int m = o.tile_m, L = o.L;
   if (!fit_tile(out.blocks, s->n, lmin(s->dt), mmax(s->dt, 1), m, L))
     return set_error(SV_EUNSUPPORTED, "a fused block does not fit a shared-memory tile");
-  BuildCtx b{s->dt, s->n, m, L, 1, 0};
-  // With a tensor-core precision mode, dense 5-qubit blocks become their own
-  // passes; the blocks between them are planned into tile passes as usual.
+  BuildCtx b{s->dt, s->n, m, L, 1, 0, o.prec};
+  // With a tensor-core precision mode, dense 5-qubit blocks run on the tensor
+  // cores: inside 12-qubit tile passes (TOP_TC ops) when the tile size is
+  // 12, otherwise as passes of their own between the tile passes.
   const bool tc = o.prec != SV_PREC_PLAIN && s->dt == SV_C64 && s->n >= 12;
+  if (tc && m == kTcTileM && o.tc_in_tile) {
+    for (Block &blk : out.blocks)
+      if (blk.kind == TOP_DENSE && blk.qubits.size() == 5 && blk.controls.empty() && !blk.diag) blk.kind = TOP_TC;
+    std::vector<PassPlan> passes = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, kMaxMatPerPass);
+    if (passes.empty() && !out.blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
+    for (const PassPlan &P : passes) SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
+    out.lay = layout_of(out.prog, 0, 0);
+    return SV_OK;
+  }
   std::vector<Block> seg;
   auto flush = [&]() -> sv_status {
     if (seg.empty()) return SV_OK;
@@ -333,6 +355,7 @@ sv_status get_program(sv_state *s, const sv_circuit *c, const double *params, co
   H.val(o.L);
   H.val(o.mode);
   H.val(o.prec);
+  H.val(o.tc_in_tile);
   H.val((int)s->dt);
   if (params && c->n_params > 0) H.bytes(params, sizeof(double) * c->n_params);
   const uint64_t key = H.h;

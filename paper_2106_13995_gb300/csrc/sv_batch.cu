@@ -109,7 +109,7 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
     uint64_t min_tiles = ~0ull;
     for (const TilePass &tp : cps[b]->prog.passes) min_tiles = std::min<uint64_t>(min_tiles, (uint64_t)1 << (tp.n - tp.m));
     bool has_tc = false;
-    for (const TilePass &tp : cps[b]->prog.passes) has_tc |= (tp.flags & kPassTC) != 0;
+    for (const TilePass &tp : cps[b]->prog.passes) has_tc |= (tp.flags & (kPassTC | kPassHasTC)) != 0;
     wide[b] = !cps[b]->prog.passes.empty() && (has_tc || min_tiles >= (uint64_t)2 * (uint64_t)s0->sm_count);
   }
   // descriptors in wave order: pass 0 of every state, then pass 1, ...
@@ -157,6 +157,7 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
         tp.coeffs = reinterpret_cast<const double *>(base + cp.lay.coeffs_off);
         tp.v0 = states[b]->amps;
         tp.nvec = 1;
+        tp.err = reinterpret_cast<uint32_t *>(states[b]->ws + kWsCtrl + kWsErrFlag);
         SV_TRY(launch_any_pass(states[b], tp, 1, st));
       }
       hkey = (hkey ^ keys[b] ^ (uint64_t)(uintptr_t)states[b]->amps) * 1099511628211ull;

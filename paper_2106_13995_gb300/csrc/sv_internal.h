@@ -46,7 +46,8 @@ enum TileOpKind : uint8_t {
   TOP_GRAD = 2,      // acc[slot] += Im <v1 | G v0>, G = X/Y/Z/P1(-2) on one local target
   TOP_PAULI = 3,     // v1[l ^ xm] += c * phase * (-1)^{popcount(l & zm)} v0[l]
   TOP_ZERO = 4,      // v1 <- 0
-  TOP_DOT = 5        // acc[slot] += Re <v0 | v1>
+  TOP_DOT = 5,       // acc[slot] += Re <v0 | v1>
+  TOP_TC = 6         // 5-qubit dense block on the tensor cores (12-qubit tiles)
 };
 
 // 32-byte op descriptor; matrices live in a separate pool.
@@ -72,6 +73,10 @@ constexpr uint8_t kGenBatchMat = 0x80;   // TileOp.gen flag: matrix from the per
 // the tensor cores; hi_pos[0..4] hold its targets, mat0 the 16-byte index of
 // its packed operand in the matrix pool, bits 9..10 the sv_prec mode.
 constexpr uint32_t kPassTC = 0x100;
+// TilePass.flags: the pass contains TOP_TC ops (allocate TMEM); mode in bits 9..10
+constexpr uint32_t kPassHasTC = 0x8;
+constexpr int kTcTileM = 12;          // tile size that gives M = 128 groups for a 5-qubit block
+size_t tc_smem_bytes(sv_prec mode);   // extra shared memory of a pass with TOP_TC ops
 struct TilePass {
   int32_t n;              // state qubits
   int32_t m;              // tile qubits
@@ -94,6 +99,7 @@ struct TilePass {
   void *const *tbl1;      // device: per-batch pointers of vector 1 (or null)
   void *v0;               // vector 0 when tbl0 is null
   void *v1;               // vector 1 when tbl1 is null
+  uint32_t *err;          // error flag for bounded waits (TOP_TC)
 };
 
 // Arguments of the persistent batch kernel (all pointers are device memory).
@@ -224,6 +230,7 @@ struct BuildCtx {
   int n, m, L;
   uint32_t nvec;
   uint32_t flags;
+  int prec = SV_PREC_PLAIN;   // mode of TOP_TC ops
 };
 sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
                     std::vector<uint32_t> &op0s, const std::vector<int> &batch_mat_off);
@@ -249,6 +256,7 @@ sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &
                          const std::vector<uint32_t> &op0s, const LaunchEnv &E);
 struct Opts {
   int fusion_k, tile_m, L, prec, mode;
+  bool tc_in_tile = false;
 };
 Opts resolve(const sv_state *s, const sv_options *o, int nvec);
 // Fill fusion_k / tile_m that the caller left at 0 from the autotuner's

@@ -19,17 +19,19 @@ def one_block_circuit(n, targets, rng):
     return c
 
 
+# tile_m 12: the block runs inside a 12-qubit tile pass; 11: as a pass of its own
+@pytest.mark.parametrize("tile_m", [12, 11])
 @pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("targets", [(0, 1, 2, 3, 4), (4, 3, 2, 1, 0), (7, 2, 11, 0, 13), (13, 12, 11, 10, 9),
                                      (1, 5, 9, 12, 3)])
-def test_single_block(svlib, oracle, mode, targets):
+def test_single_block(svlib, oracle, mode, targets, tile_m):
     rng = np.random.default_rng(sum(targets))
     n = 14
     c = one_block_circuit(n, targets, rng)
     psi0 = W.random_state(n, rng)
     cast = psi0.astype(np.complex64).astype(np.complex128)
     s = svlib.StateVector(n, "c64").load(psi0)
-    opts = svlib.options(prec=MODES[mode])
+    opts = svlib.options(prec=MODES[mode], tile_m=tile_m)
     nb, npass = s.plan_info(c, opts=opts)
     assert nb == 1 and npass == 1
     s.apply_circuit(c, opts=opts)
@@ -42,30 +44,32 @@ def test_single_block(svlib, oracle, mode, targets):
 
 
 @pytest.mark.parametrize("mode", list(MODES))
-def test_large_state_tiles(svlib, oracle, mode):
-    """Many 128-group tiles per CTA (grid-stride loop), 20 qubits."""
+@pytest.mark.parametrize("tile_m", [12, 11])
+def test_large_state_tiles(svlib, oracle, mode, tile_m):
+    """Many tiles (256 tile passes / grid-stride CTAs), 20 qubits."""
     rng = np.random.default_rng(5)
     n = 20
     c = one_block_circuit(n, (19, 3, 0, 10, 17), rng)
     psi0 = W.random_state(n, rng)
     s = svlib.StateVector(n, "c64").load(psi0)
-    s.apply_circuit(c, opts=svlib.options(prec=MODES[mode]))
+    s.apply_circuit(c, opts=svlib.options(prec=MODES[mode], tile_m=tile_m))
     want = oracle.run(c, psi0.astype(np.complex64).astype(np.complex128))
     inf, amp = fidelity_metrics(want, s.numpy())
     assert inf <= 1e-8 and amp <= AMP_TOL[mode] * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("tile_m", [12, 11])
 @pytest.mark.parametrize("mode", list(MODES))
-def test_circuits_with_fused_5q_blocks(svlib, oracle, mode):
+def test_circuits_with_fused_5q_blocks(svlib, oracle, mode, tile_m):
     for c in (W.random_u3_cz(16, 12, 3), W.grid_random(4, 4, 10, 2),
               W.remove_qubits(W.grid_random(5, 6, 8, 1), 10, 3)):
-        opts = svlib.options(prec=MODES[mode])
+        opts = svlib.options(prec=MODES[mode], tile_m=tile_m)
         s = svlib.StateVector(c.n_qubits, "c64").set_basis(0)
         nb, npass = s.plan_info(c, opts=opts)
         s.apply_circuit(c, opts=opts)
         inf, amp = fidelity_metrics(oracle.run(c), s.numpy())
         assert inf <= 1e-5, (c.name, mode, inf)
-        print(f"{c.name} {mode}: blocks {nb}, passes {npass}, 1-F {inf:.2e}, max|d| {amp:.2e}")
+        print(f"{c.name} {mode} m={tile_m}: blocks {nb}, passes {npass}, 1-F {inf:.2e}, max|d| {amp:.2e}")
 
 
 def test_tc_rejected_for_complex128(svlib, oracle):
