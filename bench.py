@@ -389,8 +389,35 @@ def main():
         tbu = timed(uneven_batched, ku) / ku
         N.check(N.lib().sv_synchronize(ust[0].h))
         tpu = timed(uneven_plain, ku) / ku
+        # fused 5-qubit blocks on the tensor cores (split-BF16 / split-TF32)
+        # vs plain complex64 per-gate passes, same batch; accuracy of each
+        # against the plain tiled complex64 result (the FP64-oracle errors
+        # are measured by the test suite)
+        modes = {"tiled_plain": sim.options(), "tc_bf16x3": sim.options(prec=N.SV_PREC_TC_BF16X3),
+                 "tc_tf32x3": sim.options(prec=N.SV_PREC_TC_TF32X3),
+                 "per_gate_plain": sim.options(fusion_k=1, mode=N.SV_MODE_PER_GATE)}
+        ref_idx = [i for i, c in enumerate(circs) if c.n_qubits in (14, 18, 22)][:6]
+        ref_states = {}
+        per_mode = {}
+        for name, mo in modes.items():
+            def run_mode(mo=mo):
+                for st_, mm in zip(ust, ums):
+                    st_.set_basis(0)
+                    st_.apply_circuit(mm, opts=mo)
+            run_mode()
+            tm_ = timed(run_mode, 1)
+            outs = {i: ust[i].numpy().astype(np.complex128) for i in ref_idx}
+            if name == "tiled_plain":
+                ref_states = outs
+            worst = 0.0
+            for i in ref_idx:
+                a, b_ = ref_states[i], outs[i]
+                f = abs(np.vdot(a, b_)) ** 2 / (np.vdot(a, a).real * np.vdot(b_, b_).real)
+                worst = max(worst, 1.0 - f)
+            per_mode[name] = {"circuits_per_s": len(circs) / tm_, "max_1mF_vs_tiled_c64": worst}
         out["uneven_batch"] = {"circuits_per_s_batched": len(circs) / tbu, "circuits_per_s_plain": len(circs) / tpu,
-                               "speedup": tpu / tbu, "circuits": len(circs), "widths": "10..24", "depth": 40,
+                               "speedup": tpu / tbu, "per_circuit_modes": per_mode,
+                               "circuits": len(circs), "widths": "10..24", "depth": 40,
                                "gates": int(sum(len(c.ops) for c in circs)),
                                "launch": "one CUDA graph per call: a persistent cooperative launch for states "
                                          "whose passes have < 2 tiles per SM, full-grid tile launches for the "

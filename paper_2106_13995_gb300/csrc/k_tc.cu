@@ -92,15 +92,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(const __grid_constan
   const uint32_t ksteps = A.mode == 1 ? kTcCols / 8 : kTcCols / 16;
 
   uint32_t phase = 0;
-  bool failed = false;
   const uint64_t ntiles = A.ngroups / kTcRows;
-  for (uint64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    // gather this thread's group and write its hi/lo row
-    const uint64_t g = tile * kTcRows + tid;
-    const uint64_t base = ins0_mask64(g, A.tmask);
-    float2 x[32];
+  // software pipeline: the next tile's amplitudes are loaded into registers
+  // while the current tile's MMAs run and its results are written back
+  uint64_t tile = blockIdx.x;
+  float2 x[32];
+  uint64_t base = 0;
+  if (tile < ntiles) {
+    base = ins0_mask64(tile * kTcRows + tid, A.tmask);
 #pragma unroll
     for (int y = 0; y < 32; y++) x[y] = __ldcs(A.amps + base + A.off[y]);
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
     if (A.mode == 1) {
 #pragma unroll
       for (int c = 0; c < 16; c++) {   // 16-byte chunk c = columns 4c .. 4c+3 = amplitudes 2c, 2c+1
@@ -151,6 +154,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(const __grid_constan
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
                    : "memory");
     }
+    // prefetch the next tile while the MMAs run
+    const uint64_t cur_base = base;
+    const uint64_t next = tile + gridDim.x;
+    float2 xn[32];
+    if (next < ntiles) {
+      base = ins0_mask64(next * kTcRows + tid, A.tmask);
+#pragma unroll
+      for (int y = 0; y < 32; y++) xn[y] = __ldcs(A.amps + base + A.off[y]);
+    }
     // thread 0 waits (bounded) and tells the others, so all take one branch
     if (tid == 0) {
       s_ok = mbar_wait(bar, phase, A.spin_limit) ? 1u : 0u;
@@ -160,19 +172,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(const __grid_constan
       }
     }
     __syncthreads();
-    if (!s_ok) {
-      failed = true;
-      break;
-    }
+    if (!s_ok) break;
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     uint32_t r[64];
     tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16), r);
 #pragma unroll
-    for (int y = 0; y < 32; y++) __stcs(A.amps + base + A.off[y], make_float2(__uint_as_float(r[2 * y]),
-                                                                             __uint_as_float(r[2 * y + 1])));
+    for (int y = 0; y < 32; y++)
+      __stcs(A.amps + cur_base + A.off[y], make_float2(__uint_as_float(r[2 * y]), __uint_as_float(r[2 * y + 1])));
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();   // TMEM and shared rows are free for the next tile
+#pragma unroll
+    for (int y = 0; y < 32; y++) x[y] = xn[y];
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();

@@ -481,19 +481,62 @@ __global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_consta
   tile_body<R, false>(P, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-// Tile passes that contain tensor-core ops: each CTA allocates its TMEM
-// columns and mbarrier once and walks over tiles (grid-stride).
+// Tile passes that contain tensor-core ops (one vector; dense, diagonal and
+// TC ops).  Each CTA allocates its TMEM columns and mbarrier once and walks
+// over tiles with two tile buffers: while it applies the ops of one tile,
+// 8-byte cp.async copies bring the next tile into the other buffer (into the
+// same swizzled slots), so HBM reads overlap the MMAs.
 constexpr int kTcTileThreads = 256;
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void tc_issue_loads(const TilePass &P, uint64_t tile, float2 *buf) {
+  const uint32_t TS = 1u << P.m, nunits = TS / 2;
+  const uint64_t base = tile_base(P, tile);
+  const uint32_t segmask = (1u << P.L) - 1;
+  const float2 *g0 = reinterpret_cast<const float2 *>(P.v0);
+  const uint32_t lthr = threadIdx.x * 2;
+  const uint64_t gthr = base | (lthr & segmask) | spread_hi(P, lthr & ~segmask);
+  const uint32_t tstep = blockDim.x * 2;
+  for (uint32_t i = 0; i * blockDim.x + threadIdx.x < nunits; i++) {
+    const uint32_t lt = i * tstep;
+    const uint64_t g = gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
+    const uint32_t l = (i * blockDim.x + threadIdx.x) * 2;
+    cp_async8(&buf[sw<float>(l)], &g0[g]);
+    cp_async8(&buf[sw<float>(l + 1)], &g0[g + 1]);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_store(const TilePass &P, uint64_t tile, const float2 *buf) {
+  const uint32_t TS = 1u << P.m, nunits = TS / 2;
+  const uint64_t base = tile_base(P, tile);
+  const uint32_t segmask = (1u << P.L) - 1;
+  float2 *g0 = reinterpret_cast<float2 *>(P.v0);
+  const uint32_t lthr = threadIdx.x * 2;
+  const uint64_t gthr = base | (lthr & segmask) | spread_hi(P, lthr & ~segmask);
+  const uint32_t tstep = blockDim.x * 2;
+  for (uint32_t i = 0; i * blockDim.x + threadIdx.x < nunits; i++) {
+    const uint32_t lt = i * tstep;
+    const uint64_t g = gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
+    const uint32_t l = (i * blockDim.x + threadIdx.x) * 2;
+    __stcs(reinterpret_cast<int4 *>(&g0[g]), Unit<float>::get(buf, l));
+  }
+}
+
 __global__ void __launch_bounds__(kTcTileThreads, 2) k_tile_tc(const __grid_constant__ TilePass P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t TS = 1u << P.m;
   const uint32_t mode = (P.flags >> 9) & 3;
   const uint32_t elem = mode == SV_PREC_TC_TF32X3 ? 4 : 2;
+  float2 *buf[2] = {reinterpret_cast<float2 *>(smem_raw), reinterpret_cast<float2 *>(smem_raw) + TS};
   TcState st;
   st.phase = 0;
   st.failed = false;
   st.T.mode = mode == SV_PREC_TC_TF32X3 ? 1u : 2u;
-  st.T.a = smem_u32(smem_raw) + (uint32_t)((size_t)P.nvec * TS * sizeof(float2));
+  st.T.a = smem_u32(smem_raw) + (uint32_t)(2 * TS * sizeof(float2));
   st.T.b = st.T.a + 2 * 128 * 64 * elem;
   st.T.bar = st.T.b + 2 * 64 * 64 * elem;
   uint32_t *slots = reinterpret_cast<uint32_t *>(smem_raw + (st.T.bar + 8 - smem_u32(smem_raw)));
@@ -511,11 +554,34 @@ __global__ void __launch_bounds__(kTcTileThreads, 2) k_tile_tc(const __grid_cons
   __syncthreads();
   tc_fence_after();
   st.T.tmem = slots[0];
+  const float2 *mats = reinterpret_cast<const float2 *>(P.mats);
   const uint64_t ntiles = 1ull << (P.n - P.m);
-  for (uint64_t t = blockIdx.x; t < ntiles && !st.failed; t += gridDim.x) {
-    tile_body<float, false, true>(P, t, 0, smem_raw, &st);
+  uint64_t t = blockIdx.x;
+  if (t < ntiles) tc_issue_loads(P, t, buf[0]);
+  for (uint32_t it = 0; t < ntiles; t += gridDim.x, it++) {
+    float2 *cur = buf[it & 1];
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
+    const uint64_t tn = t + gridDim.x;
+    if (tn < ntiles) tc_issue_loads(P, tn, buf[(it + 1) & 1]);   // overlaps with the ops below
+    const uint64_t base = tile_base(P, t);
+    for (int oi = 0; oi < P.nops; oi++) {
+      __syncthreads();
+      const TileOp op = P.ops[oi];
+      if (op.kind == TOP_TC) {
+        if (!st.failed && !tc_op(cur, op, reinterpret_cast<const uint4 *>(mats + op.mat), st.T, st.phase, P.err,
+                                 smem_raw))
+          st.failed = true;
+      } else {
+        const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);
+        if ((base & gcm) == gcm) apply_op<float>(cur, P.m, op, mats + op.mat);
+      }
+    }
+    __syncthreads();
+    if (st.failed) break;
+    tc_store(P, t, cur);
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy may outlive the CTA
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -630,7 +696,8 @@ sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStr
   if (p.flags & kPassHasTC) {
     if (s->dt != SV_C64 || p.m != kTcTileM || batch != 1)
       return set_error(SV_EINVAL, "internal: tensor-core ops need a single complex64 state and 12-qubit tiles");
-    const size_t smem = tile_smem(s->dt, p.m, (int)p.nvec) + tc_smem_bytes((sv_prec)((p.flags >> 9) & 3));
+    if (p.nvec != 1) return set_error(SV_EINVAL, "internal: tensor-core ops act on one vector");
+    const size_t smem = 2 * tile_smem(s->dt, p.m, 1) + tc_smem_bytes((sv_prec)((p.flags >> 9) & 3));
     static bool attr = false;
     if (!attr) {
       SV_CUDA(cudaFuncSetAttribute(k_tile_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
