@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--qubits", type=int, default=30,
                     help="30 = the 5x6 grid; fewer = the same grid with random qubits removed")
+    ap.add_argument("--prec", choices=("plain", "bf16x3", "tf32x3"), default="plain",
+                    help="arithmetic of the main step's fused blocks (tensor-core modes fuse 5-qubit blocks)")
     ap.add_argument("--sections", default="all",
                     help="comma list of step,e2e,roofline,single,adjoint,uneven,cpu (default all)")
     return ap.parse_args()
@@ -216,13 +218,16 @@ def main():
     m = sim.marshal(circ)
     stream = torch.cuda.current_stream(dev)
     state = sim.StateVector(n, "c64", device=dev)
+    from paper_2106_13995_gb300 import _native as NN
+    step_opts = None if args.prec == "plain" else sim.options(
+        prec=NN.SV_PREC_TC_BF16X3 if args.prec == "bf16x3" else NN.SV_PREC_TC_TF32X3)
     zz = [(0, (1 << a) | (1 << b), 1.0) for pat in W.grid_couplers(5, 6).values() for a, b in pat
           if a < n and b < n]
     shots = np.zeros(1000, dtype=np.uint64)
 
     def step():
         state.set_basis(0)
-        state.apply_circuit(m)
+        state.apply_circuit(m, opts=step_opts)
         z = state.z_all()
         e = state.expect(zz)
         nrm = state.norm2()
@@ -249,7 +254,8 @@ def main():
     out = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": config_of(circ, args)}
-    nblocks, npasses = state.plan_info(m)
+    nblocks, npasses = state.plan_info(m, opts=step_opts)
+    out["config"]["prec"] = args.prec
     out["config"]["fused_blocks"] = nblocks
     out["config"]["tile_passes"] = npasses
 
@@ -272,7 +278,7 @@ def main():
     if "roofline" in sections:
         reps = max(2, args.steps // 2)
         state.set_basis(0)
-        tc = timed(lambda: state.apply_circuit(m), reps) / reps
+        tc = timed(lambda: state.apply_circuit(m, opts=step_opts), reps) / reps
         per_launch = tc / npasses
         achieved = gate_bytes / per_launch / 1e9
         traffic = None
@@ -311,7 +317,7 @@ def main():
         def step_e2e():
             from paper_2106_13995_gb300 import _native as N
             N.check(N.lib().sv_upload(state.h, hp, state.nbytes))
-            state.apply_circuit(m)
+            state.apply_circuit(m, opts=step_opts)
             z = state.z_all()
             e = state.expect(zz)
             s = state.sample(1000, 7)
