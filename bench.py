@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--prec", choices=("plain", "bf16x3", "tf32x3"), default="plain",
                     help="arithmetic of the main step's fused blocks (tensor-core modes fuse 5-qubit blocks)")
     ap.add_argument("--sections", default="all",
-                    help="comma list of step,e2e,roofline,single,adjoint,uneven,cpu (default all)")
+                    help="comma list of step,e2e,roofline,tc,mult,single,adjoint,uneven,cpu (default all)")
     return ap.parse_args()
 
 
@@ -63,6 +63,20 @@ def workload(nq: int):
     if nq < 30:
         c = W.remove_qubits(c, 30 - nq, seed=101)
     return c
+
+
+def max_over_ranks(t: float, dist, device) -> float:
+    """Slowest rank's time (every rank gets it)."""
+    import torch
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(units_per_rank: float, world: int, t: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time
+    (replicas: every rank processes the same fixed work)."""
+    return units_per_rank * world / t
 
 
 def measured_peaks():
@@ -212,7 +226,7 @@ def main():
     from paper_2106_13995_gb300 import sim
 
     sections = set(args.sections.split(",")) if args.sections != "all" else \
-        {"step", "e2e", "roofline", "single", "adjoint", "uneven", "cpu"}
+        {"step", "e2e", "roofline", "tc", "mult", "single", "adjoint", "uneven", "cpu"}
     circ = workload(args.qubits)
     n = circ.n_qubits
     m = sim.marshal(circ)
@@ -246,9 +260,7 @@ def main():
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         if world > 1:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+            t = max_over_ranks(t, dist, dev)
         return t
 
     out = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -266,7 +278,7 @@ def main():
     with ClockSampler(local) as clk:
         t = timed(step, args.steps)
     launches = sim.kernel_launches() - l0
-    out["value"] = len(circ.ops) * args.steps * world / t
+    out["value"] = job_value(len(circ.ops) * args.steps, world, t)
     out["ms_per_step"] = 1e3 * t / args.steps
     out["gpu_launches"] = int(launches)
     out["clocks"] = clk.summary()
@@ -294,6 +306,46 @@ def main():
                            "frac": achieved / peak, "traffic": traffic, "kernel": "k_tile<float> (tile pass)",
                            "algorithmic_bytes_per_launch": gate_bytes, "launches_per_circuit": npasses,
                            "avg_launch_ms": per_launch * 1e3, "peak_source": peak_src}
+
+    # ---- the same circuit with fused 5-qubit blocks on the tensor cores ----------
+    if "tc" in sections:
+        modes = {}
+        for name, code in (("tf32x3", NN.SV_PREC_TC_TF32X3), ("bf16x3", NN.SV_PREC_TC_BF16X3)):
+            o = sim.options(prec=code)
+            nb_, np_ = state.plan_info(m, opts=o)
+            state.set_basis(0)
+            state.apply_circuit(m, opts=o)
+            reps = max(2, args.steps // 2)
+            t_ = timed(lambda: state.apply_circuit(m, opts=o), reps) / reps
+            modes[name] = {"gates_per_s": len(circ.ops) / t_, "ms_per_circuit": 1e3 * t_, "fused_blocks": nb_,
+                           "passes": np_}
+        out["tensor_core_modes"] = modes
+
+    # ---- 29-qubit quantum multiplier: 64 basis inputs, then superposed inputs ---
+    if "mult" in sections:
+        mc = W.multiplier(7)
+        mh = W.multiplier(7, hadamard_inputs=True)
+        mmc, mmh = sim.marshal(mc), sim.marshal(mh)
+        rng = np.random.default_rng(2)
+        ab = rng.integers(0, 128, size=(64, 2))
+        del_state = state
+        ms_ = sim.StateVector(29, "c64", device=dev)
+
+        def mult_all():
+            for a_, b_ in ab:
+                ms_.set_basis(W.multiplier_basis_index(int(a_), int(b_), 7))
+                ms_.apply_circuit(mmc)
+
+        mult_all()
+        tm_ = timed(mult_all, 1)
+        ms_.set_basis(0)
+        ms_.apply_circuit(mmh)
+        th_ = timed(lambda: (ms_.set_basis(0), ms_.apply_circuit(mmh)), 2) / 2
+        out["multiplier"] = {"n_qubits": 29, "native_ops": len(mc.ops), "basis_runs": 64,
+                             "runs_per_s": 64 / tm_, "gates_per_s": 64 * len(mc.ops) / tm_,
+                             "superposed_run_ms": 1e3 * th_, "passes": ms_.plan_info(mmc)[1]}
+        ms_.close()
+        del del_state
 
     # ---- single-gate passes per target (K1-K3) ---------------------------------
     if "single" in sections:

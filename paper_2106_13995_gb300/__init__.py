@@ -9,7 +9,7 @@ from . import _native  # noqa: F401
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from .buildlib import build as _b
     return _b(force=force)
 
 

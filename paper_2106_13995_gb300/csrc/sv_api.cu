@@ -287,7 +287,20 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
     seg.clear();
     return SV_OK;
   };
-  for (const Block &blk : out.blocks) {
+  for (const Block &blk0 : out.blocks) {
+    Block blk = blk0;
+    // a dense 4-qubit block would be the slowest op of a tile pass on CUDA
+    // cores: pad it with an idle qubit (U x I) and run it on the tensor cores
+    if (tc && blk.kind == TOP_DENSE && blk.qubits.size() == 4 && blk.controls.empty() && !blk.diag) {
+      int extra = 0;
+      while (std::find(blk.qubits.begin(), blk.qubits.end(), extra) != blk.qubits.end()) extra++;
+      std::vector<cd> U5(32 * 32, 0.0);
+      for (int r = 0; r < 32; r++)
+        for (int c = 0; c < 32; c++)
+          if ((r >> 4) == (c >> 4)) U5[(size_t)r * 32 + c] = blk.U[(size_t)(r & 15) * 16 + (c & 15)];
+      blk.U = U5;
+      blk.qubits.push_back(extra);
+    }
     const bool is_tc = tc && blk.kind == TOP_DENSE && blk.qubits.size() == 5 && blk.controls.empty() && !blk.diag;
     if (!is_tc) {
       seg.push_back(blk);

@@ -1,0 +1,77 @@
+"""Host logic without a GPU: the library's fusion planner, tile-pass planner
+and program emitter, linked from its object files into a small CPU
+interpreter of the emitted programs (tests/host/plan_emulator.cu), must
+reproduce the FP64 oracle for every fusion width and tile size, with
+controls inside and outside the tile."""
+import ctypes as C
+import glob
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module")
+def emu():
+    import paper_2106_13995_gb300 as P
+    import importlib
+    B = importlib.import_module("paper_2106_13995_gb300.buildlib")
+    P.build()
+    objs = sorted(glob.glob(os.path.join(B.OUT_DIR, "*.o")))
+    out_dir = os.path.join(HERE, "host", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "libplanemu.so")
+    src = os.path.join(HERE, "host", "plan_emulator.cu")
+    deps = [src] + objs
+    if not os.path.exists(lib) or any(os.path.getmtime(d) > os.path.getmtime(lib) for d in deps):
+        subprocess.check_call([B.nvcc(), *B.ARCH, "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                               "-I", os.path.join(ROOT, "include"), "-o", lib, src, *objs])
+    L = C.CDLL(lib)
+    L.plan_emulate.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
+    return L
+
+
+def run(emu, circ, fk, m, L):
+    from paper_2106_13995_gb300 import sim
+    mm = sim.marshal(circ)
+    psi = np.zeros(1 << circ.n_qubits, dtype=np.complex128)
+    psi[0] = 1
+    nb = C.c_int()
+    npass = emu.plan_emulate(C.addressof(mm.c), psi.ctypes.data, fk, m, L, C.byref(nb))
+    assert npass > 0
+    return psi, npass, nb.value
+
+
+@pytest.mark.parametrize("fk", [1, 2, 3, 4, 6])
+def test_mixed_circuits_every_fusion_and_tile(emu, oracle, fk):
+    for seed in range(6):
+        n = 9 + seed % 3
+        c = W.random_gate_circuit(n, 60, seed=seed * 7 + fk)
+        want = oracle.run(c)
+        for m, L in ((n, 3), (7, 1), (8, 3)):
+            got, npass, nb = run(emu, c, fk, m, L)
+            assert oracle.infidelity(want, got) <= 1e-12, (seed, fk, m, L)
+
+
+def test_grid_and_multiplier(emu, oracle):
+    for c in (W.grid_random(3, 4, 8, 3), W.multiplier(2), W.random_u3_cz(11, 6, 2)):
+        want = oracle.run(c)
+        for fk, m in ((3, 8), (2, 6), (5, 10)):
+            got, npass, nb = run(emu, c, fk, min(m, c.n_qubits), 2)
+            assert oracle.infidelity(want, got) <= 1e-12, (c.name, fk, m)
+
+
+def test_fusion_reduces_blocks(emu):
+    """Fusion merges gates into fewer blocks (pass counts may go either way:
+    wider blocks pack less freely into a tile's free slots)."""
+    c = W.grid_random(4, 4, 10, 1)
+    _, p1, b1 = run(emu, c, 1, 8, 3)
+    _, p3, b3 = run(emu, c, 3, 8, 3)
+    assert b3 < b1 == len(c.ops)
+    assert p1 > 0 and p3 > 0
