@@ -285,6 +285,30 @@ def main():
     gate_bytes = 2 * (1 << n) * 8
     out["hbm_gbs_effective"] = len(circ.ops) * gate_bytes * args.steps / t / 1e9
 
+    # ---- end to end through the C ABI from host buffers -----------------------
+    if "e2e" in sections:
+        host = torch.zeros(2 << n, dtype=torch.float32, pin_memory=True)
+        host[0] = 1.0
+        hp = host.data_ptr()
+
+        def step_e2e():
+            from paper_2106_13995_gb300 import _native as N
+            N.check(N.lib().sv_upload(state.h, hp, state.nbytes))
+            state.apply_circuit(m, opts=step_opts)
+            z = state.z_all()
+            e = state.expect(zz)
+            s = state.sample(1000, 7)
+            return z, e, s
+
+        for _ in range(max(1, args.warmup)):
+            step_e2e()
+        ke = max(2, args.steps // 2)
+        te = timed(step_e2e, ke)
+        out["e2e"] = {"value": len(circ.ops) * ke * world / te, "unit": UNIT,
+                      "h2d_bytes_per_step": state.nbytes, "d2h_bytes_per_step": 8 * n + 8 + 8 * 1000,
+                      "ms_per_step": 1e3 * te / ke}
+        del host
+
     # ---- roofline of the dominant kernel (the tile pass) -----------------------
     peak, peak_src = measured_peaks()
     if "roofline" in sections:
@@ -359,30 +383,6 @@ def main():
                                    "min_gbs": min(vals), "mean_gbs": statistics.mean(vals),
                                    "min_frac_of_measured": min(vals) / peak,
                                    "gates_per_s_min": min(vals) * 1e9 / gate_bytes}
-
-    # ---- end to end through the C ABI from host buffers -----------------------
-    if "e2e" in sections:
-        host = torch.zeros(2 << n, dtype=torch.float32, pin_memory=True)
-        host[0] = 1.0
-        hp = host.data_ptr()
-
-        def step_e2e():
-            from paper_2106_13995_gb300 import _native as N
-            N.check(N.lib().sv_upload(state.h, hp, state.nbytes))
-            state.apply_circuit(m, opts=step_opts)
-            z = state.z_all()
-            e = state.expect(zz)
-            s = state.sample(1000, 7)
-            return z, e, s
-
-        for _ in range(max(1, args.warmup)):
-            step_e2e()
-        ke = max(2, args.steps // 2)
-        te = timed(step_e2e, ke)
-        out["e2e"] = {"value": len(circ.ops) * ke * world / te, "unit": UNIT,
-                      "h2d_bytes_per_step": state.nbytes, "d2h_bytes_per_step": 8 * n + 8 + 8 * 1000,
-                      "ms_per_step": 1e3 * te / ke}
-        del host
 
     # ---- adjoint gradients, batched vs plain (20-qubit ansatz, 64 sets) ----------
     if "adjoint" in sections:
