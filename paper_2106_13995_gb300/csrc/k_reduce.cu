@@ -150,31 +150,85 @@ template <typename R> struct ExpectArgs {
   R fr[kMaxGroupTerms], fi[kMaxGroupTerms];
 };
 
+// Term t's sign at index x is (-1)^{Y_t(x)}, Y_t(x) = parity(x & z_t).  The
+// map x -> Y(x) (one bit per term) is linear over GF(2), so Y(x) is the XOR of
+// five per-byte tables of x; the group's factor f(x) = sum_t f_t (-1)^{Y_t}
+// is the sum of per-byte tables of Y.  A warp sweeps runs of 256 consecutive
+// amplitudes: the high bytes of x are fixed over a run, so each amplitude
+// costs one x-table lookup and one lookup per 8 terms instead of a parity and
+// a select per term.
+constexpr int kExpectXBytes = 5;   // n <= 40
+
 template <typename R>
-__global__ void k_expect(const typename Cx<R>::T *__restrict__ a, uint64_t namps,
-                         const __grid_constant__ ExpectArgs<R> A, double *partial) {
+__global__ void __launch_bounds__(kRedThreads) k_expect(const typename Cx<R>::T *__restrict__ a, uint64_t namps,
+                                                        const __grid_constant__ ExpectArgs<R> A, double *partial) {
   using C = typename Cx<R>::T;
-  constexpr int RUN = 16;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  double acc = 0;
-  for (uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x0 < namps; x0 += RUN * stride) {
-    R run = 0;
-#pragma unroll 4
-    for (int j = 0; j < RUN; j++) {
-      const uint64_t x = x0 + j * stride;
-      if (x >= namps) break;
-      const C v = a[x], w = a[x ^ A.xm];
-      R fr = 0, fi = 0;
-      for (int t = 0; t < A.nt; t++) {
-        const bool neg = __popcll(x & A.zm[t]) & 1;
-        fr += neg ? -A.fr[t] : A.fr[t];
-        fi += neg ? -A.fi[t] : A.fi[t];
-      }
-      // Re(conj(w) * (f * v))
-      const R pr = fr * v.x - fi * v.y, pi = fr * v.y + fi * v.x;
-      run += w.x * pr + w.y * pi;
+  __shared__ uint64_t sCol[8 * kExpectXBytes];
+  __shared__ uint64_t sT[kExpectXBytes][256];
+  __shared__ C sW[kMaxGroupTerms / 8][256];
+  const int tid = threadIdx.x;
+  // column of qubit q: the terms whose z mask contains q
+  for (int q = tid; q < 8 * kExpectXBytes; q += blockDim.x) {
+    uint64_t col = 0;
+    for (int t = 0; t < A.nt; t++) col |= ((A.zm[t] >> q) & 1ull) << t;
+    sCol[q] = col;
+  }
+  // signed coefficient sums of each byte value of Y (bit set: -f_t, clear: +f_t)
+  const int nyb = (A.nt + 7) >> 3;
+  for (int e = tid; e < nyb * 256; e += blockDim.x) {
+    const int j = e >> 8, v = e & 255;
+    R wr = 0, wi = 0;
+    for (int b = 0; b < 8; b++) {
+      const int t = 8 * j + b;
+      if (t >= A.nt) break;
+      const R sg = ((v >> b) & 1) ? R(-1) : R(1);
+      wr += sg * A.fr[t];
+      wi += sg * A.fi[t];
     }
-    acc += (double)run;
+    sW[j][v] = cmake(wr, wi);
+  }
+  __syncthreads();
+  for (int e = tid; e < kExpectXBytes * 256; e += blockDim.x) {
+    const int k = e >> 8, v = e & 255;
+    uint64_t y = 0;
+    for (int b = 0; b < 8; b++)
+      if ((v >> b) & 1) y ^= sCol[8 * k + b];
+    sT[k][v] = y;
+  }
+  __syncthreads();
+
+  const int lane = tid & 31;
+  const uint64_t nruns = (namps + 255) >> 8;
+  const uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  double acc = 0;
+  for (uint64_t run = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (tid >> 5); run < nruns; run += wstride) {
+    const uint64_t x0 = run << 8;
+    uint64_t yhi = 0;
+#pragma unroll
+    for (int k = 1; k < kExpectXBytes; k++) yhi ^= sT[k][(x0 >> (8 * k)) & 255];
+    R part = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const uint32_t lo = 32 * j + lane;
+      const uint64_t x = x0 + lo;
+      if (x < namps) {
+        const uint64_t y = yhi ^ sT[0][lo];
+        R fr = 0, fi = 0;
+#pragma unroll
+        for (int q = 0; q < kMaxGroupTerms / 8; q++) {
+          if (q < nyb) {
+            const C w8 = sW[q][(y >> (8 * q)) & 255];
+            fr += w8.x;
+            fi += w8.y;
+          }
+        }
+        const C v = a[x], w = a[x ^ A.xm];
+        // Re(conj(w) * (f * v))
+        const R pr = fr * v.x - fi * v.y, pi = fr * v.y + fi * v.x;
+        part += w.x * pr + w.y * pi;
+      }
+    }
+    acc += (double)part;
   }
   block_sum_to(acc, partial + blockIdx.x);
 }
@@ -196,7 +250,7 @@ static sv_status expect_launch(sv_state *s, uint64_t xm, const uint64_t *zm, con
   }
   const uint64_t na = 1ull << s->n;
   double *partial = reinterpret_cast<double *>(s->ws + kWsRed);
-  const int g = red_grid(s, na / 16 + 1);
+  const int g = red_grid(s, na / 64 + 1);
   k_expect<R><<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const typename Cx<R>::T *>(s->amps), na, A,
                                                 partial);
   k_finalize<<<1, 32, 0, s->stream>>>(partial, g, 1, out_dev);

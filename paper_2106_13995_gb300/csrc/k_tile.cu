@@ -26,77 +26,156 @@
 
 namespace sv {
 
-constexpr int kTileMaxThreads = 512;
+constexpr int kTileMaxThreads = 512;    // persistent batch kernel
+// tile passes: at most 256 threads (larger tiles give each thread more
+// amplitudes), at least three CTAs per SM, which leaves up to 80 registers
+constexpr int kTilePassThreads = 256;
+#ifndef SV_TILE_MINB
+#define SV_TILE_MINB 4
+#endif
+#ifndef SV_TILE_INLINE
+#define SV_TILE_INLINE 1
+#endif
+#ifndef SV_K3_UNROLL
+#define SV_K3_UNROLL 1
+#endif
+#ifndef SV_K3_G
+#define SV_K3_G 2
+#endif
+#ifndef SV_TRIP_F
+#define SV_TRIP_F 0
+#endif
+constexpr int kTilePassMinBlocks = SV_TILE_MINB;
 
 // swizzled shared-memory slot of tile amplitude l (a bijection on [0, 2^m))
 template <typename R> __device__ __forceinline__ uint32_t sw(uint32_t l);
 template <> __device__ __forceinline__ uint32_t sw<float>(uint32_t l) { return l ^ ((l >> 4) & 15u); }
 template <> __device__ __forceinline__ uint32_t sw<double>(uint32_t l) { return l ^ ((l >> 3) & 7u); }
 
+// byte offset of tile amplitude l in the swizzled layout.  The swizzle is
+// linear over GF(2), so swb(a ^ b) = swb(a) ^ swb(b): the offset of a group
+// member is the group base's offset XOR a per-op constant.
+template <typename R> __device__ __forceinline__ uint32_t swb(uint32_t l) {
+  return sw<R>(l) * (uint32_t)sizeof(typename Cx<R>::T);
+}
+
+// State index of tile t's amplitude 0 and of local bits above the L
+// contiguous qubits; only set bits cost work.
 __device__ __forceinline__ uint64_t tile_base(const TilePass &P, uint64_t t) {
   uint64_t base = 0;
-  const int nout = P.n - P.m;
-  for (int j = 0; j < nout; j++) base |= ((t >> j) & 1ull) << P.out_pos[j];
+  for (; t; t &= t - 1) base |= 1ull << P.out_pos[__ffsll((long long)t) - 1];
   return base;
 }
 
 __device__ __forceinline__ uint64_t spread_hi(const TilePass &P, uint32_t l) {
   uint64_t g = 0;
-  for (int b = P.L; b < P.m; b++) g |= (uint64_t)((l >> b) & 1u) << P.hi_pos[b - P.L];
+  for (uint32_t x = l >> P.L; x; x &= x - 1) g |= 1ull << P.hi_pos[__ffs(x) - 1];
   return g;
 }
 
+// two consecutive complex entries of a matrix row (16-byte aligned for c64)
+__device__ __forceinline__ void ld_pair(const float2 *p, float2 &a, float2 &b) {
+  const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+  a = make_float2(q.x, q.y);
+  b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void ld_pair(const double2 *p, double2 &a, double2 &b) {
+  a = __ldg(p);
+  b = __ldg(p + 1);
+}
+
 // Dense block on K local targets (U row-major complex in global memory,
-// read through L1).  Matrices of 1-2 qubits are held in registers for the
-// whole op; larger ones are read per use, each load serving G groups.
+// read through L1).  Group g's members sit at swb(base(g)) ^ soff[y]; with a
+// power-of-two block size the thread's part of base(g) is computed once per
+// op and each trip adds a warp-uniform part.  Matrices of 1-2 qubits stay in
+// registers for the whole op; larger ones are read per row, each 16-byte load
+// serving G groups.
 template <typename R, int K, int G>
 __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
                                          const typename Cx<R>::T *__restrict__ U) {
   using C = typename Cx<R>::T;
   constexpr int D = 1 << K;
   constexpr bool kRegU = K <= 2;
-  uint32_t off[D];
+  constexpr bool kUnrollRows = K <= 2 || (K == 3 && SV_K3_UNROLL);
+  unsigned char *vb = reinterpret_cast<unsigned char *>(v);
+  uint32_t soff[D], e[K], tmask = 0;
+  soff[0] = 0;
 #pragma unroll
-  for (int y = 0; y < D; y++) {
-    uint32_t o = 0;
+  for (int j = 0; j < K; j++) {
+    const uint32_t bit = 1u << op.t[j];
+    tmask |= bit;
+    e[j] = swb<R>(bit);
 #pragma unroll
-    for (int j = 0; j < K; j++) o |= (uint32_t)((y >> j) & 1) << op.t[j];
-    off[y] = o;
+    for (int y = 0; y < (1 << j); y++) soff[y + (1 << j)] = soff[y] ^ e[j];
   }
   C ur[kRegU ? D * D : 1];
   if constexpr (kRegU) {
 #pragma unroll
-    for (int e = 0; e < D * D; e++) ur[e] = __ldg(&U[e]);
+    for (int q = 0; q < D * D; q += 2) ld_pair(U + q, ur[q], ur[q + 1]);
   }
-  const uint32_t fixed = off[D - 1] | op.lcmask;
+  const uint32_t fixed = tmask | op.lcmask;
   const uint32_t ngroups = 1u << (m - __popc(fixed));
-  const uint32_t step = blockDim.x * G;
-  for (uint32_t g0 = threadIdx.x; g0 < ngroups; g0 += step) {
-    uint32_t i0[G];
+  const uint32_t T = blockDim.x;
+  if (threadIdx.x >= ngroups) return;
+  // thread t's groups are t + c T, c < ntrips; base(t + c T) = base(t) ^ D(c)
+  // with D linear in c: D(c) = XOR of f[j] over the set bits j of c
+  const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
+  const uint32_t sthr = swb<R>(ins0_mask(threadIdx.x, fixed) | op.lcmask);
+#if SV_TRIP_F
+  uint32_t f[5];
+#pragma unroll
+  for (int j = 0; j < 5; j++) f[j] = (ntrips >> j) > 1 ? swb<R>(ins0_mask(T << j, fixed)) : 0u;
+#endif
+  for (uint32_t c0 = 0; c0 < ntrips; c0 += G) {
+    uint32_t s[G];
     bool ok[G];
     C x[G][D];
 #pragma unroll
     for (int h = 0; h < G; h++) {
-      const uint32_t g = g0 + h * blockDim.x;
-      ok[h] = g < ngroups;
-      i0[h] = ins0_mask(ok[h] ? g : 0, fixed) | op.lcmask;
+      const uint32_t cc = c0 + h;
+      ok[h] = cc < ntrips;
+#if SV_TRIP_F
+      uint32_t dc = 0;
 #pragma unroll
-      for (int y = 0; y < D; y++) x[h][y] = v[sw<R>(i0[h] + off[y])];
+      for (int j = 0; j < 5; j++) dc ^= ((cc >> j) & 1) ? f[j] : 0u;
+      s[h] = sthr ^ (ok[h] ? dc : 0u);
+#else
+      s[h] = sthr ^ swb<R>(ins0_mask(ok[h] ? cc * T : 0u, fixed));
+#endif
+#pragma unroll
+      for (int y = 0; y < D; y++) x[h][y] = *reinterpret_cast<const C *>(vb + (s[h] ^ soff[y]));
     }
-#pragma unroll(kRegU ? D : 1)
+#pragma unroll(kUnrollRows ? D : 1)
     for (int r = 0; r < D; r++) {
       C a[G];
 #pragma unroll
       for (int h = 0; h < G; h++) a[h] = czero<C>();
 #pragma unroll
-      for (int y = 0; y < D; y++) {
-        const C u = kRegU ? ur[(r * D + y) % (kRegU ? D * D : 1)] : __ldg(&U[r * D + y]);
+      for (int y = 0; y < D; y += 2) {
+        C u0, u1;
+        if constexpr (kRegU) {
+          u0 = ur[(r * D + y) % (kRegU ? D * D : 1)];
+          u1 = ur[(r * D + y + 1) % (kRegU ? D * D : 1)];
+        } else {
+          ld_pair(U + r * D + y, u0, u1);
+        }
 #pragma unroll
-        for (int h = 0; h < G; h++) a[h] = cfma(u, x[h][y], a[h]);
+        for (int h = 0; h < G; h++) {
+          a[h] = cfma(u0, x[h][y], a[h]);
+          a[h] = cfma(u1, x[h][y + 1], a[h]);
+        }
+      }
+      uint32_t so;
+      if constexpr (kUnrollRows) {
+        so = soff[r % D];
+      } else {
+        so = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++) so ^= ((r >> j) & 1) ? e[j] : 0u;
       }
 #pragma unroll
       for (int h = 0; h < G; h++)
-        if (ok[h]) v[sw<R>(i0[h] + off[r])] = a[h];
+        if (ok[h]) *reinterpret_cast<C *>(vb + (s[h] ^ so)) = a[h];
     }
   }
 }
@@ -104,39 +183,66 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
 // Dense blocks of 4..6 qubits keep 2^k amplitudes per thread; they live in
 // separate functions so their register pressure does not spill the k <= 3
 // paths that make up most passes.
-template <typename R, int K>
-__device__ __noinline__ void dense_op_big(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
-                                          const typename Cx<R>::T *__restrict__ U) {
-  dense_op<R, K, 1>(v, m, op, U);
+// Each dense op runs as a function of its own, so its registers do not add
+// to those the tile loop keeps live; the op is read from global memory here,
+// so no caller keeps an addressable (local-memory) copy of it.
+template <typename R, int K, int G>
+__device__ __noinline__ void dense_op_nl(typename Cx<R>::T *__restrict__ v, int m, const TileOp *gop,
+                                         const typename Cx<R>::T *__restrict__ U) {
+  const TileOp op = *gop;
+  dense_op<R, K, G>(v, m, op, U);
 }
 
+// Diagonal block: amplitude l is multiplied by d[r(l)], r(l) the target bits
+// of l.  Both the slot and r are linear in l, so each splits into a thread
+// part and a warp-uniform trip part.
 template <typename R>
 __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
                                         const typename Cx<R>::T *__restrict__ d) {
+  using C = typename Cx<R>::T;
+  unsigned char *vb = reinterpret_cast<unsigned char *>(v);
   const uint32_t ngroups = 1u << (m - __popc(op.lcmask));
-  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
-    const uint32_t l = ins0_mask(g, op.lcmask) | op.lcmask;
+  const uint32_t T = blockDim.x;
+  if (threadIdx.x >= ngroups) return;
+  uint32_t tpos[6];
+#pragma unroll
+  for (int j = 0; j < 6; j++) tpos[j] = op.t[j];
+  const int k = op.k;
+  auto rows = [&](uint32_t l) {
     uint32_t r = 0;
-    for (int j = 0; j < op.k; j++) r |= ((l >> op.t[j]) & 1u) << j;
-    const uint32_t p = sw<R>(l);
-    v[p] = cmul(__ldg(&d[r]), v[p]);
+#pragma unroll
+    for (int j = 0; j < 6; j++)
+      if (j < k) r |= ((l >> tpos[j]) & 1u) << j;
+    return r;
+  };
+  const uint32_t lthr = ins0_mask(threadIdx.x, op.lcmask) | op.lcmask;
+  const uint32_t sthr = swb<R>(lthr), rthr = rows(lthr);
+  for (uint32_t g0 = 0; g0 < ngroups; g0 += T) {
+    const uint32_t lg = ins0_mask(g0, op.lcmask);
+    C *p = reinterpret_cast<C *>(vb + (sthr ^ swb<R>(lg)));
+    *p = cmul(__ldg(&d[rthr ^ rows(lg)]), *p);
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const TileOp &op,
+// NL: every dense op out of line (kernels whose own state leaves few
+// registers for an inlined op)
+template <typename R, bool NL = !SV_TILE_INLINE>
+__device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const TileOp &op, const TileOp *gop,
                                          const typename Cx<R>::T *U) {
   if (op.kind == TOP_DIAG) {
     diag_op<R>(v, m, op, U);
     return;
   }
   switch (op.k) {
-    case 1: dense_op<R, 1, 2>(v, m, op, U); break;
-    case 2: dense_op<R, 2, 1>(v, m, op, U); break;
-    case 3: dense_op<R, 3, sizeof(R) == 4 ? 2 : 1>(v, m, op, U); break;
-    case 4: dense_op_big<R, 4>(v, m, op, U); break;
-    case 5: dense_op_big<R, 5>(v, m, op, U); break;
-    default: dense_op_big<R, 6>(v, m, op, U); break;
+    case 1: if (NL) dense_op_nl<R, 1, 2>(v, m, gop, U); else dense_op<R, 1, 2>(v, m, op, U); break;
+    case 2: if (NL) dense_op_nl<R, 2, 1>(v, m, gop, U); else dense_op<R, 2, 1>(v, m, op, U); break;
+    case 3:
+      if (NL) dense_op_nl<R, 3, sizeof(R) == 4 ? SV_K3_G : 1>(v, m, gop, U);
+      else dense_op<R, 3, sizeof(R) == 4 ? SV_K3_G : 1>(v, m, op, U);
+      break;
+    case 4: dense_op_nl<R, 4, 1>(v, m, gop, U); break;
+    case 5: dense_op_nl<R, 5, 1>(v, m, gop, U); break;
+    default: dense_op_nl<R, 6, 1>(v, m, gop, U); break;
   }
 }
 
@@ -184,124 +290,6 @@ __device__ void grad_op(const typename Cx<R>::T *__restrict__ psi,
   block_acc<R>(part, acc + op.slot);
 }
 
-// ---- TOP_TC: 5-qubit block on the tensor cores inside a 12-qubit tile -----
-// The tile's 128 groups of 32 amplitudes form the A operand (hi/lo parts of
-// every real column, canonical K-major layout), the packed real embedding of
-// U is the B operand (staged from global memory per op), D (128 x 64 FP32)
-// lives in TMEM.  See k_tc.cu for the operand formats.
-struct TcShared {
-  uint32_t a;        // shared address of A_hi (A_lo follows)
-  uint32_t b;        // shared address of B_hi (B_lo follows)
-  uint32_t bar;      // mbarrier
-  uint32_t tmem;     // TMEM base address
-  uint32_t mode;     // 1 = TF32 x3, 2 = BF16 x3
-  uint32_t *ok;      // shared flag: the MMAs completed
-};
-
-__device__ __forceinline__ uint32_t tf32_part(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
-
-// returns false if the MMA wait ran out (error flag raised)
-__device__ __noinline__ bool tc_op(float2 *__restrict__ v, const TileOp &op, const uint4 *__restrict__ bglob,
-                                   const TcShared &T, uint32_t &phase, uint32_t *err, unsigned char *smem) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const uint32_t elem = T.mode == 1 ? 4 : 2;
-  const uint32_t a_bytes = 128 * 64 * elem, b_bytes = 64 * 64 * elem;
-  unsigned char *sm_a = smem + (T.a - smem_u32(smem));
-  unsigned char *sm_b = smem + (T.b - smem_u32(smem));
-  // B operand
-  for (uint32_t i = tid; i < 2 * b_bytes / 16; i += nthr) reinterpret_cast<uint4 *>(sm_b)[i] = __ldg(bglob + i);
-  uint32_t offs[32], tmask = 0;
-#pragma unroll
-  for (int y = 0; y < 32; y++) {
-    uint32_t o = 0;
-#pragma unroll
-    for (int j = 0; j < 5; j++) o |= (uint32_t)((y >> j) & 1) << op.t[j];
-    offs[y] = o;
-  }
-  tmask = offs[31];
-  // A operand: item = (row, quarter of its 32 amplitudes)
-  for (int item = tid; item < 512; item += nthr) {
-    const uint32_t row = item >> 2, q = item & 3;
-    const uint32_t i0 = ins0_mask(row, tmask);
-    float2 x[8];
-#pragma unroll
-    for (int e = 0; e < 8; e++) x[e] = v[sw<float>(i0 + offs[8 * q + e])];
-    if (T.mode == 1) {
-#pragma unroll
-      for (int c = 0; c < 4; c++) {          // 16-byte chunk (4q + c): amplitudes 8q + 2c, +1
-        const float f[4] = {x[2 * c].x, x[2 * c].y, x[2 * c + 1].x, x[2 * c + 1].y};
-        uint4 hi, lo;
-        hi.x = tf32_part(f[0]); hi.y = tf32_part(f[1]); hi.z = tf32_part(f[2]); hi.w = tf32_part(f[3]);
-        lo.x = __float_as_uint(f[0] - __uint_as_float(hi.x));
-        lo.y = __float_as_uint(f[1] - __uint_as_float(hi.y));
-        lo.z = __float_as_uint(f[2] - __uint_as_float(hi.z));
-        lo.w = __float_as_uint(f[3] - __uint_as_float(hi.w));
-        const uint32_t o = cm_offset(row, 4 * q + c, 128);
-        *reinterpret_cast<uint4 *>(sm_a + o) = hi;
-        *reinterpret_cast<uint4 *>(sm_a + a_bytes + o) = lo;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < 2; c++) {          // 16-byte chunk (2q + c): amplitudes 8q + 4c .. +3
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-          const float2 a = x[4 * c + e];
-          const __nv_bfloat16 hr = __float2bfloat16_rn(a.x), hi_ = __float2bfloat16_rn(a.y);
-          const __nv_bfloat16 lr = __float2bfloat16_rn(a.x - __bfloat162float(hr));
-          const __nv_bfloat16 li = __float2bfloat16_rn(a.y - __bfloat162float(hi_));
-          hw[e] = (uint32_t)__bfloat16_as_ushort(hr) | ((uint32_t)__bfloat16_as_ushort(hi_) << 16);
-          lw[e] = (uint32_t)__bfloat16_as_ushort(lr) | ((uint32_t)__bfloat16_as_ushort(li) << 16);
-        }
-        const uint32_t o = cm_offset(row, 2 * q + c, 128);
-        *reinterpret_cast<uint4 *>(sm_a + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4 *>(sm_a + a_bytes + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      }
-    }
-  }
-  fence_async_smem();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (tid == 0) {
-    const uint32_t idesc = instr_desc(T.mode == 1 ? 2u : 1u);
-    const uint32_t ksteps = T.mode == 1 ? 8 : 4;
-    const uint32_t a_lbo = 128 * 16, b_lbo = 64 * 16;
-    const uint32_t as[3] = {T.a, T.a, T.a + a_bytes}, bs[3] = {T.b, T.b + b_bytes, T.b};
-    for (int t = 0; t < 3; t++)
-      for (uint32_t k = 0; k < ksteps; k++)
-        mma_issue(T.tmem, smem_desc(as[t] + k * 2 * a_lbo, a_lbo, 128), smem_desc(bs[t] + k * 2 * b_lbo, b_lbo, 128),
-                  idesc, (t > 0 || k > 0) ? 1u : 0u, T.mode);
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(T.bar)
-                 : "memory");
-    const bool ok = mbar_wait(T.bar, phase, 1u << 22);
-    if (!ok) {
-      atomicExch(err, 1u);
-      mbar_wait(T.bar, phase, 1u << 22);
-    }
-    *T.ok = ok ? 1u : 0u;
-  }
-  __syncthreads();
-  phase ^= 1u;
-  if (!*T.ok) return false;
-  tc_fence_after();
-  // epilogue: warp w reads lanes 32 (w % 4) .. +31 (rows) and a share of the
-  // 64 columns; 16 columns = 8 amplitudes per read
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
-  const int lq = warp & 3, cgroups = nwarps >> 2;
-  const uint32_t row = 32 * lq + lane;
-  const uint32_t i0 = ins0_mask(row, tmask);
-  for (int cg = warp >> 2; cg < 4; cg += cgroups) {
-    uint32_t r[16];
-    tmem_ld16(T.tmem + ((uint32_t)(32 * lq) << 16) + 16 * cg, r);
-#pragma unroll
-    for (int e = 0; e < 8; e++)
-      v[sw<float>(i0 + offs[8 * cg + e])] = make_float2(__uint_as_float(r[2 * e]), __uint_as_float(r[2 * e + 1]));
-  }
-  tc_fence_before();
-  return true;
-}
-
 // 16-byte unit u of the tile <-> shared memory (swizzled amplitude slots)
 template <typename R> struct Unit;
 template <> struct Unit<float> {
@@ -331,15 +319,8 @@ template <> struct Unit<double> {
 // The work of one CTA on one tile.  COH selects L2-coherent loads and stores
 // (bypassing L1), needed when other CTAs of the same launch wrote the tile
 // earlier (the persistent batch kernel); otherwise streaming hints are used.
-struct TcState {
-  TcShared T;
-  uint32_t phase;
-  bool failed;
-};
-
-template <typename R, bool COH, bool TC = false>
-__device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int b, unsigned char *smem_raw,
-                                          TcState *tcs = nullptr) {
+template <typename R, bool COH>
+__device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int b, unsigned char *smem_raw) {
   using C = typename Cx<R>::T;
   const uint32_t TS = 1u << P.m;
   C *v0 = reinterpret_cast<C *>(smem_raw);
@@ -402,20 +383,12 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
       case TOP_DIAG: {
         if ((base & gcm) != gcm) break;
         const C *U = ((op.gen & kGenBatchMat) ? pmats : mats) + op.mat;
-        if (op.vmask & 1) apply_op<R>(v0, P.m, op, U);
-        if (op.vmask & 2) apply_op<R>(v1, P.m, op, U);
+        if (op.vmask & 1) apply_op<R>(v0, P.m, op, P.ops + oi, U);
+        if (op.vmask & 2) apply_op<R>(v1, P.m, op, P.ops + oi, U);
         break;
       }
       case TOP_GRAD:
         grad_op<R>(v0, v1, P.m, op, acc);
-        break;
-      case TOP_TC:
-        if constexpr (TC && sizeof(R) == 4) {
-          if (!tcs->failed && !tc_op(reinterpret_cast<float2 *>(v0), op,
-                                     reinterpret_cast<const uint4 *>(mats + op.mat), tcs->T, tcs->phase, P.err,
-                                     smem_raw))
-            tcs->failed = true;
-        }
         break;
       case TOP_PAULI: {
         const uint32_t xm = (uint16_t)op.slot;
@@ -457,9 +430,6 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
     }
   }
   __syncthreads();
-  if constexpr (TC) {
-    if (tcs->failed) return;   // the tile is incomplete: leave HBM as it was
-  }
   const bool store0 = !(P.flags & 2u), store1 = P.nvec > 1 && !(P.flags & 4u);
   for (uint32_t i = 0; i * blockDim.x + threadIdx.x < nunits; i++) {
     const uint32_t l = (i * blockDim.x + threadIdx.x) * UN::APU;
@@ -476,117 +446,326 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kTileMaxThreads, 2) k_tile(const __grid_constant__ TilePass P) {
+__global__ void __launch_bounds__(kTilePassThreads, kTilePassMinBlocks) k_tile(const __grid_constant__ TilePass P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   tile_body<R, false>(P, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-// Tile passes that contain tensor-core ops (one vector; dense, diagonal and
-// TC ops).  Each CTA allocates its TMEM columns and mbarrier once and walks
-// over tiles with two tile buffers: while it applies the ops of one tile,
-// 8-byte cp.async copies bring the next tile into the other buffer (into the
-// same swizzled slots), so HBM reads overlap the MMAs.
-constexpr int kTcTileThreads = 256;
+// ---------------------------------------------------------------------------
+// Tile passes with tensor-core blocks (complex64, 12-qubit tiles).
+//
+// A fused dense 5-qubit block acting on a 4096-amplitude tile is the product
+// of the tile's 128 groups of 32 amplitudes (rows, as 64 reals each) with the
+// real 64 x 64 embedding [[Re U, Im U], [-Im U, Re U]]^T of U: one
+// M = 128, N = 64, K = 64 GEMM, done in split precision as
+// A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation.
+//
+// Data flow per op and tile: thread t of the CTA's four warps reads row t's
+// 32 amplitudes from the shared-memory tile, splits them into hi/lo parts and
+// writes them straight into its own TMEM lane (tcgen05.st), where the MMAs
+// read A; B (the packed matrix) comes from shared memory, loaded by one bulk
+// copy per op and prefetched one op ahead; D lands in TMEM and thread t
+// reads its row back (tcgen05.ld) and scatters it into the tile.  Shared
+// memory therefore carries only the gather, the scatter and B, and three
+// CTAs share an SM, so one CTA's MMAs overlap the others' gathers, scatters
+// and HBM traffic.  Dense blocks of 1-3 qubits and diagonal blocks of the
+// same pass run on the CUDA cores in the same tile.
+//
+// Every wait is bounded; a wait that runs out raises the error flag, the CTA
+// stops storing tiles, waits (bounded) for its own copies and MMAs, frees
+// its TMEM and returns.
+// ---------------------------------------------------------------------------
+constexpr int kTcThreads = 256;   // two warps per TMEM lane quadrant
+constexpr uint32_t kTcSpin = 1u << 22;
 
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]), "r"(r[32])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// D (TMEM) = A (TMEM) x B (shared memory, descriptor)
+__device__ __forceinline__ void mma_tmem_a(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc,
+                                           bool tf32) {
+  if (tf32)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void tc_issue_loads(const TilePass &P, uint64_t tile, float2 *buf) {
-  const uint32_t TS = 1u << P.m, nunits = TS / 2;
-  const uint64_t base = tile_base(P, tile);
-  const uint32_t segmask = (1u << P.L) - 1;
-  const float2 *g0 = reinterpret_cast<const float2 *>(P.v0);
-  const uint32_t lthr = threadIdx.x * 2;
-  const uint64_t gthr = base | (lthr & segmask) | spread_hi(P, lthr & ~segmask);
-  const uint32_t tstep = blockDim.x * 2;
-  for (uint32_t i = 0; i * blockDim.x + threadIdx.x < nunits; i++) {
-    const uint32_t lt = i * tstep;
-    const uint64_t g = gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
-    const uint32_t l = (i * blockDim.x + threadIdx.x) * 2;
-    cp_async8(&buf[sw<float>(l)], &g0[g]);
-    cp_async8(&buf[sw<float>(l + 1)], &g0[g + 1]);
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t tf32_hi(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
+
+// next TOP_TC op after op index `oi` (wrapping to the pass's first one), -1 if none
+__device__ __forceinline__ int next_tc_op(const TilePass &P, int oi) {
+  for (int k = 1; k <= P.nops; k++) {
+    const int j = (oi + k) % P.nops;
+    if (P.ops[j].kind == TOP_TC) return j;
   }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  return -1;
 }
 
-__device__ __forceinline__ void tc_store(const TilePass &P, uint64_t tile, const float2 *buf) {
-  const uint32_t TS = 1u << P.m, nunits = TS / 2;
-  const uint64_t base = tile_base(P, tile);
+// 16-byte units of tile `tile` <-> the swizzled shared-memory tile (one vector)
+template <bool STORE>
+__device__ __forceinline__ void tc_tile_io(const TilePass &P, uint64_t tile, float2 *v) {
+  const uint32_t nunits = (1u << P.m) / 2;
   const uint32_t segmask = (1u << P.L) - 1;
   float2 *g0 = reinterpret_cast<float2 *>(P.v0);
+  const uint64_t base = tile_base(P, tile);
   const uint32_t lthr = threadIdx.x * 2;
   const uint64_t gthr = base | (lthr & segmask) | spread_hi(P, lthr & ~segmask);
   const uint32_t tstep = blockDim.x * 2;
-  for (uint32_t i = 0; i * blockDim.x + threadIdx.x < nunits; i++) {
-    const uint32_t lt = i * tstep;
-    const uint64_t g = gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
-    const uint32_t l = (i * blockDim.x + threadIdx.x) * 2;
-    __stcs(reinterpret_cast<int4 *>(&g0[g]), Unit<float>::get(buf, l));
+  constexpr int BATCH = 8;
+  for (uint32_t i0 = 0; i0 * blockDim.x < nunits; i0 += BATCH) {
+    int4 r[BATCH];
+    uint64_t g[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; j++) {
+      const uint32_t lt = (i0 + j) * tstep;
+      g[j] = gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
+    }
+    if constexpr (STORE) {
+#pragma unroll
+      for (int j = 0; j < BATCH; j++) {
+        const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
+        if (u < nunits) __stcs(reinterpret_cast<int4 *>(&g0[g[j]]), Unit<float>::get(v, u * 2));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < BATCH; j++) {
+        const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
+        if (u < nunits) r[j] = __ldcs(reinterpret_cast<const int4 *>(&g0[g[j]]));
+      }
+#pragma unroll
+      for (int j = 0; j < BATCH; j++) {
+        const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
+        if (u < nunits) Unit<float>::put(v, u * 2, r[j]);
+      }
+    }
   }
 }
 
-__global__ void __launch_bounds__(kTcTileThreads, 2) k_tile_tc(const __grid_constant__ TilePass P) {
+struct TcCta {
+  uint32_t tmem;       // TMEM base (lane 0, first allocated column)
+  uint32_t bufs;       // shared address of the two B buffers
+  uint32_t bar_b;      // two mbarriers: B buffer 0 / 1 loaded
+  uint32_t bar_mma;    // mbarrier: the op's MMAs completed
+  uint32_t *flag;      // shared: the last wait succeeded
+  bool tf32;
+  uint32_t bbytes;     // B hi + lo
+  uint32_t a_lo, d;    // TMEM column offsets of A_lo and D (A_hi at 0)
+};
+
+// One TOP_TC op on the tile; j = this CTA's count of TC ops so far.
+// Returns false if a wait ran out.
+// Thread 0 tracks what it has in flight: pend_b = the TC op index whose B
+// load has not been waited for, pend_mma = the op whose MMAs have not (or
+// kNone).
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool tc_tile_op(const TilePass &P, const TileOp &op, float2 *v, const TcCta &c,
+                                           uint32_t j, int next_op, bool more, uint32_t &pend_b,
+                                           uint32_t &pend_mma) {
+  unsigned char *vb = reinterpret_cast<unsigned char *>(v);
+  // warp w serves TMEM lanes (rows) 32 (w % 4) .. + 31 and amplitudes
+  // 16 (w / 4) .. + 15 of each row
+  const int tid = threadIdx.x, warp = tid >> 5, quad = warp & 3, half = warp >> 2;
+  const uint32_t row = 32 * quad + (tid & 31);
+  uint32_t tmask = 0, e[5];
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    const uint32_t bit = 1u << op.t[q];
+    tmask |= bit;
+    e[q] = swb<float>(bit);
+  }
+  uint32_t soff[16];   // slots of amplitudes 16 half + y, y < 16
+  soff[0] = swb<float>(ins0_mask(row, tmask)) ^ (half ? e[4] : 0u);
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int y = 0; y < (1 << q); y++) soff[y + (1 << q)] = soff[y] ^ e[q];
+  const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
+  // gather + split, straight into the rows' TMEM lanes
+  if (c.tf32) {
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      uint32_t hi[16], lo[16];
+#pragma unroll
+      for (int y = 0; y < 8; y++) {
+        const float2 a = *reinterpret_cast<const float2 *>(vb + soff[8 * h + y]);
+        hi[2 * y] = tf32_hi(a.x);
+        hi[2 * y + 1] = tf32_hi(a.y);
+        lo[2 * y] = __float_as_uint(a.x - __uint_as_float(hi[2 * y]));
+        lo[2 * y + 1] = __float_as_uint(a.y - __uint_as_float(hi[2 * y + 1]));
+      }
+      tmem_st16(c.tmem + lane_base + 32 * half + 16 * h, hi);
+      tmem_st16(c.tmem + lane_base + c.a_lo + 32 * half + 16 * h, lo);
+    }
+  } else {
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int y = 0; y < 16; y++) {
+      const float2 a = *reinterpret_cast<const float2 *>(vb + soff[y]);
+      const __nv_bfloat162 hb = __floats2bfloat162_rn(a.x, a.y);
+      const float2 hf = __bfloat1622float2(hb);
+      const __nv_bfloat162 lb = __floats2bfloat162_rn(a.x - hf.x, a.y - hf.y);
+      hi[y] = *reinterpret_cast<const uint32_t *>(&hb);
+      lo[y] = *reinterpret_cast<const uint32_t *>(&lb);
+    }
+    tmem_st16(c.tmem + lane_base + 16 * half, hi);
+    tmem_st16(c.tmem + lane_base + c.a_lo + 16 * half, lo);
+  }
+  tmem_wait_st();
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc_fence_after();
+    const uint32_t buf = j & 1;
+    bool ok = mbar_wait(c.bar_b + 8 * buf, (j >> 1) & 1, kTcSpin);
+    if (ok) {
+      pend_b = kNone;
+      const uint32_t idesc = instr_desc(c.tf32 ? 2u : 1u);
+      const uint32_t ksteps = c.tf32 ? 8 : 4;
+      const uint32_t half = c.bbytes / 2, b_lbo = 64 * 16;
+      const uint32_t bh = c.bufs + buf * c.bbytes;
+      const uint32_t as[3] = {0, 0, c.a_lo}, bs[3] = {bh, bh + half, bh};
+      for (int t = 0; t < 3; t++)
+        for (uint32_t k = 0; k < ksteps; k++)
+          mma_tmem_a(c.tmem + c.d, c.tmem + as[t] + 8 * k, smem_desc(bs[t] + k * 2 * b_lbo, b_lbo, 128), idesc,
+                     (t > 0 || k > 0) ? 1u : 0u, c.tf32);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       c.bar_mma)
+                   : "memory");
+      pend_mma = j;
+      // prefetch the next TC op's B into the other buffer (its last reader,
+      // op j - 1, has completed)
+      if (more && next_op >= 0) {
+        const float2 *mats = reinterpret_cast<const float2 *>(P.mats);
+        bulk_load(c.bufs + (buf ^ 1) * c.bbytes, mats + P.ops[next_op].mat, c.bbytes, c.bar_b + 8 * (buf ^ 1));
+        pend_b = j + 1;
+      }
+      ok = mbar_wait(c.bar_mma, j & 1, kTcSpin);
+      if (ok) pend_mma = kNone;
+    }
+    if (!ok) atomicExch(P.err, 1u);
+    *c.flag = ok ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!*c.flag) return false;
+  tc_fence_after();
+  uint32_t r[32];
+  tmem_ld32(c.tmem + lane_base + c.d + 32 * half, r);
+#pragma unroll
+  for (int y = 0; y < 16; y++)
+    *reinterpret_cast<float2 *>(vb + soff[y]) = make_float2(__uint_as_float(r[2 * y]), __uint_as_float(r[2 * y + 1]));
+  tc_fence_before();
+  return true;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 3) k_tile_tc(const __grid_constant__ TilePass P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t TS = 1u << P.m;
-  const uint32_t mode = (P.flags >> 9) & 3;
-  const uint32_t elem = mode == SV_PREC_TC_TF32X3 ? 4 : 2;
-  float2 *buf[2] = {reinterpret_cast<float2 *>(smem_raw), reinterpret_cast<float2 *>(smem_raw) + TS};
-  TcState st;
-  st.phase = 0;
-  st.failed = false;
-  st.T.mode = mode == SV_PREC_TC_TF32X3 ? 1u : 2u;
-  st.T.a = smem_u32(smem_raw) + (uint32_t)(2 * TS * sizeof(float2));
-  st.T.b = st.T.a + 2 * 128 * 64 * elem;
-  st.T.bar = st.T.b + 2 * 64 * 64 * elem;
-  uint32_t *slots = reinterpret_cast<uint32_t *>(smem_raw + (st.T.bar + 8 - smem_u32(smem_raw)));
-  st.T.ok = slots + 1;
+  float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+  TcCta c;
+  c.tf32 = ((P.flags >> 9) & 3) == SV_PREC_TC_TF32X3;
+  c.bbytes = 2 * 64 * 64 * (c.tf32 ? 4 : 2);
+  c.a_lo = c.tf32 ? 64 : 32;
+  c.d = c.tf32 ? 128 : 64;
+  const uint32_t ncols = c.tf32 ? 256 : 128;
+  c.bufs = smem_u32(smem_raw) + TS * (uint32_t)sizeof(float2);
+  c.bar_b = c.bufs + 2 * c.bbytes;
+  c.bar_mma = c.bar_b + 16;
+  uint32_t *slots = reinterpret_cast<uint32_t *>(smem_raw + (c.bar_mma + 8 - smem_u32(smem_raw)));
+  c.flag = slots + 1;
+  const uint64_t ntiles = 1ull << (P.n - P.m);
+  const int first_tc = next_tc_op(P, P.nops - 1);
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(st.T.bar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(c.bar_b));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(c.bar_b + 8));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(c.bar_mma));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (threadIdx.x < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slots)),
-                 "r"(64u));
+                 "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  st.T.tmem = slots[0];
+  c.tmem = slots[0];
+  // B of the first TC op
+  uint32_t pend_b = kNone, pend_mma = kNone;
+  if (threadIdx.x == 0 && first_tc >= 0 && blockIdx.x < ntiles) {
+    bulk_load(c.bufs, reinterpret_cast<const float2 *>(P.mats) + P.ops[first_tc].mat, c.bbytes, c.bar_b);
+    pend_b = 0;
+  }
   const float2 *mats = reinterpret_cast<const float2 *>(P.mats);
-  const uint64_t ntiles = 1ull << (P.n - P.m);
-  uint64_t t = blockIdx.x;
-  if (t < ntiles) tc_issue_loads(P, t, buf[0]);
-  for (uint32_t it = 0; t < ntiles; t += gridDim.x, it++) {
-    float2 *cur = buf[it & 1];
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();
-    const uint64_t tn = t + gridDim.x;
-    if (tn < ntiles) tc_issue_loads(P, tn, buf[(it + 1) & 1]);   // overlaps with the ops below
+  uint32_t j = 0;   // TC ops done by this CTA
+  bool failed = false;
+  for (uint64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    tc_tile_io<false>(P, t, tile);
     const uint64_t base = tile_base(P, t);
-    for (int oi = 0; oi < P.nops; oi++) {
+    const bool more_tiles = t + gridDim.x < ntiles;
+    for (int oi = 0; oi < P.nops && !failed; oi++) {
       __syncthreads();
       const TileOp op = P.ops[oi];
       if (op.kind == TOP_TC) {
-        if (!st.failed && !tc_op(cur, op, reinterpret_cast<const uint4 *>(mats + op.mat), st.T, st.phase, P.err,
-                                 smem_raw))
-          st.failed = true;
+        const int nx = next_tc_op(P, oi);
+        const bool more = nx > oi || more_tiles;   // a later TC op in this tile, or a next tile
+        if (!tc_tile_op(P, op, tile, c, j, nx, more, pend_b, pend_mma)) failed = true;
+        j++;
       } else {
         const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);
-        if ((base & gcm) == gcm) apply_op<float>(cur, P.m, op, mats + op.mat);
+        if ((base & gcm) == gcm) apply_op<float, true>(tile, P.m, op, P.ops + oi, mats + op.mat);
       }
     }
     __syncthreads();
-    if (st.failed) break;
-    tc_store(P, t, cur);
+    if (!failed) tc_tile_io<true>(P, t, tile);
   }
-  asm volatile("cp.async.wait_all;\n" ::: "memory");   // no copy may outlive the CTA
+  // no copy or MMA may outlive the CTA
+  if (threadIdx.x == 0) {
+    if (pend_mma != kNone) mbar_wait(c.bar_mma, pend_mma & 1, kTcSpin);
+    if (pend_b != kNone) mbar_wait(c.bar_b + 8 * (pend_b & 1), (pend_b >> 1) & 1, kTcSpin);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(st.T.tmem), "r"(64u));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(c.tmem), "r"(ncols));
+}
+
+size_t tc_tile_smem(sv_prec mode) {
+  const size_t bbytes = 2 * 64 * 64 * (mode == SV_PREC_TC_TF32X3 ? 4 : 2);
+  return ((size_t)1 << kTcTileM) * 8 + 2 * bbytes + 64;
 }
 
 // ---------------------------------------------------------------------------
@@ -676,15 +855,11 @@ int tile_threads(int m, sv_dtype dt) {
   const int units = (1 << m) / (dt == SV_C64 ? 2 : 1);
   int t = units / 8;
   if (t < 32) t = 32;
-  if (t > kTileMaxThreads) t = kTileMaxThreads;
+  if (t > kTilePassThreads) t = kTilePassThreads;
   return t;
 }
 
 size_t tile_smem(sv_dtype dt, int m, int nvec) { return (size_t)nvec * ((size_t)1 << m) * amp_bytes(dt); }
-size_t tc_smem_bytes(sv_prec mode) {
-  const size_t elem = mode == SV_PREC_TC_TF32X3 ? 4 : 2;
-  return 2 * 128 * 64 * elem + 2 * 64 * 64 * elem + 16;
-}
 
 
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
@@ -694,20 +869,23 @@ sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
 sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream) {
   static bool attr_set[2][64] = {};
   if (p.flags & kPassHasTC) {
-    if (s->dt != SV_C64 || p.m != kTcTileM || batch != 1)
-      return set_error(SV_EINVAL, "internal: tensor-core ops need a single complex64 state and 12-qubit tiles");
-    if (p.nvec != 1) return set_error(SV_EINVAL, "internal: tensor-core ops act on one vector");
-    const size_t smem = 2 * tile_smem(s->dt, p.m, 1) + tc_smem_bytes((sv_prec)((p.flags >> 9) & 3));
+    if (s->dt != SV_C64 || p.m != kTcTileM || batch != 1 || p.nvec != 1)
+      return set_error(SV_EINVAL, "internal: tensor-core tile pass needs one complex64 vector and 12-qubit tiles");
+    const sv_prec mode = (sv_prec)((p.flags >> 9) & 3);
+    const size_t smem = tc_tile_smem(mode);
     static bool attr = false;
     if (!attr) {
       SV_CUDA(cudaFuncSetAttribute(k_tile_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+      SV_CUDA(cudaFuncSetAttribute(k_tile_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
       attr = true;
     }
-    int per_sm = 0;
-    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_tc, kTcTileThreads, smem));
+    // CTAs per SM: shared memory and TMEM admit three (BF16 operands, 128
+    // TMEM columns each) or two (TF32, 256 columns); the grid strides over the
+    // tiles, so CTAs that do not fit at once simply start later
+    const uint64_t per_sm = mode == SV_PREC_TC_TF32X3 ? 2 : 3;
     const uint64_t ntiles = 1ull << (p.n - p.m);
-    const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)std::max(1, per_sm) * s->sm_count);
-    k_tile_tc<<<grid, kTcTileThreads, smem, stream>>>(p);
+    const int grid = (int)std::min<uint64_t>(ntiles, per_sm * (uint64_t)s->sm_count);
+    k_tile_tc<<<grid, kTcThreads, smem, stream>>>(p);
     g_launches++;
     SV_CUDA(cudaGetLastError());
     return SV_OK;

@@ -136,6 +136,7 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
         op.gen = kGenBatchMat;
         op.mat = (uint32_t)batch_mat_off[blk.inst];
       } else {
+        while (prog.mats.size() % 16) prog.mats.push_back(0);   // rows are read 16 bytes at a time
         op.mat = (uint32_t)(prog.mats.size() / ab);
         const int d = 1 << op.k;
         if (op.kind == TOP_DIAG) {
@@ -269,9 +270,24 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
   // cores: inside 12-qubit tile passes (TOP_TC ops) when the tile size is
   // 12, otherwise as passes of their own between the tile passes.
   const bool tc = o.prec != SV_PREC_PLAIN && s->dt == SV_C64 && s->n >= 12;
+  // a dense 4-qubit block would be the slowest op of a tile pass on CUDA
+  // cores: pad it with an idle qubit (U x I) and run it on the tensor cores
+  auto pad4 = [](Block &blk) {
+    if (!(blk.kind == TOP_DENSE && blk.qubits.size() == 4 && blk.controls.empty() && !blk.diag)) return;
+    int extra = 0;
+    while (std::find(blk.qubits.begin(), blk.qubits.end(), extra) != blk.qubits.end()) extra++;
+    std::vector<cd> U5(32 * 32, 0.0);
+    for (int r = 0; r < 32; r++)
+      for (int c = 0; c < 32; c++)
+        if ((r >> 4) == (c >> 4)) U5[(size_t)r * 32 + c] = blk.U[(size_t)(r & 15) * 16 + (c & 15)];
+    blk.U = U5;
+    blk.qubits.push_back(extra);
+  };
   if (tc && m == kTcTileM && o.tc_in_tile) {
-    for (Block &blk : out.blocks)
+    for (Block &blk : out.blocks) {
+      pad4(blk);
       if (blk.kind == TOP_DENSE && blk.qubits.size() == 5 && blk.controls.empty() && !blk.diag) blk.kind = TOP_TC;
+    }
     std::vector<PassPlan> passes = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, kMaxMatPerPass);
     if (passes.empty() && !out.blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
     for (const PassPlan &P : passes) SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
@@ -289,18 +305,7 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
   };
   for (const Block &blk0 : out.blocks) {
     Block blk = blk0;
-    // a dense 4-qubit block would be the slowest op of a tile pass on CUDA
-    // cores: pad it with an idle qubit (U x I) and run it on the tensor cores
-    if (tc && blk.kind == TOP_DENSE && blk.qubits.size() == 4 && blk.controls.empty() && !blk.diag) {
-      int extra = 0;
-      while (std::find(blk.qubits.begin(), blk.qubits.end(), extra) != blk.qubits.end()) extra++;
-      std::vector<cd> U5(32 * 32, 0.0);
-      for (int r = 0; r < 32; r++)
-        for (int c = 0; c < 32; c++)
-          if ((r >> 4) == (c >> 4)) U5[(size_t)r * 32 + c] = blk.U[(size_t)(r & 15) * 16 + (c & 15)];
-      blk.U = U5;
-      blk.qubits.push_back(extra);
-    }
+    if (tc) pad4(blk);
     const bool is_tc = tc && blk.kind == TOP_DENSE && blk.qubits.size() == 5 && blk.controls.empty() && !blk.diag;
     if (!is_tc) {
       seg.push_back(blk);

@@ -76,7 +76,7 @@ constexpr uint32_t kPassTC = 0x100;
 // TilePass.flags: the pass contains TOP_TC ops (allocate TMEM); mode in bits 9..10
 constexpr uint32_t kPassHasTC = 0x8;
 constexpr int kTcTileM = 12;          // tile size that gives M = 128 groups for a 5-qubit block
-size_t tc_smem_bytes(sv_prec mode);   // extra shared memory of a pass with TOP_TC ops
+size_t tc_tile_smem(sv_prec mode);    // shared memory of a 12-qubit tile pass with TOP_TC ops
 struct TilePass {
   int32_t n;              // state qubits
   int32_t m;              // tile qubits
