@@ -326,23 +326,56 @@ def main():
                 traffic = tr["dram_bytes_per_launch"]
         except Exception:
             traffic = None
+        kernel = {"plain": "k_tile<float> (tile pass)",
+                  "bf16x3": "k_tile_tc (tile pass with tensor-core 5-qubit blocks)",
+                  "tf32x3": "k_tile<float> and k_dense_tc (tile passes and tensor-core passes)"}[args.prec]
+        if args.prec != "plain":
+            traffic = None    # the stored capture is of the plain tile pass
         out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                           "frac": achieved / peak, "traffic": traffic, "kernel": "k_tile<float> (tile pass)",
+                           "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                            "algorithmic_bytes_per_launch": gate_bytes, "launches_per_circuit": npasses,
                            "avg_launch_ms": per_launch * 1e3, "peak_source": peak_src}
 
     # ---- the same circuit with fused 5-qubit blocks on the tensor cores ----------
     if "tc" in sections:
+        # accuracy of each mode against the plain FP32 path on the same 30-qubit
+        # circuit: 1 - |<psi_plain|psi_tc>|^2 / (|psi_plain|^2 |psi_tc|^2), FP64
+        ref = sim.StateVector(n, "c64", device=dev)
+        ref.set_basis(0)
+        ref.apply_circuit(m)
+
+        def infid(a, b):
+            va = torch.view_as_complex(a.amps.view(-1, 2))
+            vb = torch.view_as_complex(b.amps.view(-1, 2))
+            ov = torch.zeros((), dtype=torch.complex128, device=dev)
+            na = torch.zeros((), dtype=torch.float64, device=dev)
+            nb = torch.zeros((), dtype=torch.float64, device=dev)
+            step_ = 1 << 26
+            for i in range(0, va.numel(), step_):
+                x = va[i:i + step_].to(torch.complex128)
+                y = vb[i:i + step_].to(torch.complex128)
+                ov += torch.vdot(x, y)
+                na += (x.abs() ** 2).sum()
+                nb += (y.abs() ** 2).sum()
+            return float(1 - abs(ov.item()) ** 2 / (na.item() * nb.item()))
+
         modes = {}
+        arrangement = {"tf32x3": "5-qubit blocks as tensor-core passes of their own between tile passes",
+                       "bf16x3": "5-qubit blocks on the tensor cores inside 12-qubit tile passes"}
         for name, code in (("tf32x3", NN.SV_PREC_TC_TF32X3), ("bf16x3", NN.SV_PREC_TC_BF16X3)):
             o = sim.options(prec=code)
             nb_, np_ = state.plan_info(m, opts=o)
             state.set_basis(0)
             state.apply_circuit(m, opts=o)
+            torch.cuda.synchronize()
+            one_minus_f = infid(ref, state)
             reps = max(2, args.steps // 2)
             t_ = timed(lambda: state.apply_circuit(m, opts=o), reps) / reps
             modes[name] = {"gates_per_s": len(circ.ops) / t_, "ms_per_circuit": 1e3 * t_, "fused_blocks": nb_,
-                           "passes": np_}
+                           "passes": np_, "arrangement": arrangement[name],
+                           "one_minus_fidelity_vs_plain_fp32": one_minus_f,
+                           "hbm_gbs_effective": len(circ.ops) * gate_bytes / t_ / 1e9}
+        ref.close()
         out["tensor_core_modes"] = modes
 
     # ---- 29-qubit quantum multiplier: 64 basis inputs, then superposed inputs ---

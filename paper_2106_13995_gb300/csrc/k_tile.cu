@@ -28,24 +28,9 @@ namespace sv {
 
 constexpr int kTileMaxThreads = 512;    // persistent batch kernel
 // tile passes: at most 256 threads (larger tiles give each thread more
-// amplitudes), at least three CTAs per SM, which leaves up to 80 registers
+// amplitudes), four CTAs per SM (64 registers a thread)
 constexpr int kTilePassThreads = 256;
-#ifndef SV_TILE_MINB
-#define SV_TILE_MINB 4
-#endif
-#ifndef SV_TILE_INLINE
-#define SV_TILE_INLINE 1
-#endif
-#ifndef SV_K3_UNROLL
-#define SV_K3_UNROLL 1
-#endif
-#ifndef SV_K3_G
-#define SV_K3_G 2
-#endif
-#ifndef SV_TRIP_F
-#define SV_TRIP_F 0
-#endif
-constexpr int kTilePassMinBlocks = SV_TILE_MINB;
+constexpr int kTilePassMinBlocks = 4;
 
 // swizzled shared-memory slot of tile amplitude l (a bijection on [0, 2^m))
 template <typename R> __device__ __forceinline__ uint32_t sw(uint32_t l);
@@ -57,6 +42,24 @@ template <> __device__ __forceinline__ uint32_t sw<double>(uint32_t l) { return 
 // member is the group base's offset XOR a per-op constant.
 template <typename R> __device__ __forceinline__ uint32_t swb(uint32_t l) {
   return sw<R>(l) * (uint32_t)sizeof(typename Cx<R>::T);
+}
+
+// shared-memory access by 32-bit address (the tile's slots)
+__device__ __forceinline__ float2 lds_c(uint32_t a, const float2 *) {
+  float2 r;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(r.x), "=f"(r.y) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ double2 lds_c(uint32_t a, const double2 *) {
+  double2 r;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(r.x), "=d"(r.y) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ void sts_c(uint32_t a, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts_c(uint32_t a, double2 v) {
+  asm volatile("st.shared.v2.f64 [%0], {%1, %2};\n" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
 }
 
 // State index of tile t's amplitude 0 and of local bits above the L
@@ -96,8 +99,8 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
   using C = typename Cx<R>::T;
   constexpr int D = 1 << K;
   constexpr bool kRegU = K <= 2;
-  constexpr bool kUnrollRows = K <= 2 || (K == 3 && SV_K3_UNROLL);
-  unsigned char *vb = reinterpret_cast<unsigned char *>(v);
+  constexpr bool kUnrollRows = K <= 3;
+  const uint32_t vs = smem_u32(v);
   uint32_t soff[D], e[K], tmask = 0;
   soff[0] = 0;
 #pragma unroll
@@ -121,11 +124,6 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
   // with D linear in c: D(c) = XOR of f[j] over the set bits j of c
   const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
   const uint32_t sthr = swb<R>(ins0_mask(threadIdx.x, fixed) | op.lcmask);
-#if SV_TRIP_F
-  uint32_t f[5];
-#pragma unroll
-  for (int j = 0; j < 5; j++) f[j] = (ntrips >> j) > 1 ? swb<R>(ins0_mask(T << j, fixed)) : 0u;
-#endif
   for (uint32_t c0 = 0; c0 < ntrips; c0 += G) {
     uint32_t s[G];
     bool ok[G];
@@ -134,16 +132,11 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
     for (int h = 0; h < G; h++) {
       const uint32_t cc = c0 + h;
       ok[h] = cc < ntrips;
-#if SV_TRIP_F
-      uint32_t dc = 0;
-#pragma unroll
-      for (int j = 0; j < 5; j++) dc ^= ((cc >> j) & 1) ? f[j] : 0u;
-      s[h] = sthr ^ (ok[h] ? dc : 0u);
-#else
       s[h] = sthr ^ swb<R>(ins0_mask(ok[h] ? cc * T : 0u, fixed));
-#endif
 #pragma unroll
-      for (int y = 0; y < D; y++) x[h][y] = *reinterpret_cast<const C *>(vb + (s[h] ^ soff[y]));
+      for (int y = 0; y < D; y++) {
+        x[h][y] = lds_c(vs + (s[h] ^ soff[y]), (const C *)nullptr);
+      }
     }
 #pragma unroll(kUnrollRows ? D : 1)
     for (int r = 0; r < D; r++) {
@@ -175,7 +168,9 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
       }
 #pragma unroll
       for (int h = 0; h < G; h++)
-        if (ok[h]) *reinterpret_cast<C *>(vb + (s[h] ^ so)) = a[h];
+        if (ok[h]) {
+          sts_c(vs + (s[h] ^ so), a[h]);
+        }
     }
   }
 }
@@ -183,14 +178,15 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
 // Dense blocks of 4..6 qubits keep 2^k amplitudes per thread; they live in
 // separate functions so their register pressure does not spill the k <= 3
 // paths that make up most passes.
-// Each dense op runs as a function of its own, so its registers do not add
-// to those the tile loop keeps live; the op is read from global memory here,
-// so no caller keeps an addressable (local-memory) copy of it.
-template <typename R, int K, int G>
-__device__ __noinline__ void dense_op_nl(typename Cx<R>::T *__restrict__ v, int m, const TileOp *gop,
-                                         const typename Cx<R>::T *__restrict__ U) {
+// Dense blocks of 4..6 qubits keep 2^k amplitudes per thread; they run as
+// functions of their own so their registers do not crowd the k <= 3 paths
+// that make up most passes.  The op is read from global memory here, so no
+// caller keeps an addressable (local-memory) copy of it.
+template <typename R, int K>
+__device__ __noinline__ void dense_op_big(typename Cx<R>::T *__restrict__ v, int m, const TileOp *gop,
+                                          const typename Cx<R>::T *__restrict__ U) {
   const TileOp op = *gop;
-  dense_op<R, K, G>(v, m, op, U);
+  dense_op<R, K, 1>(v, m, op, U);
 }
 
 // Diagonal block: amplitude l is multiplied by d[r(l)], r(l) the target bits
@@ -224,9 +220,7 @@ __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m
   }
 }
 
-// NL: every dense op out of line (kernels whose own state leaves few
-// registers for an inlined op)
-template <typename R, bool NL = !SV_TILE_INLINE>
+template <typename R>
 __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const TileOp &op, const TileOp *gop,
                                          const typename Cx<R>::T *U) {
   if (op.kind == TOP_DIAG) {
@@ -234,15 +228,12 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
     return;
   }
   switch (op.k) {
-    case 1: if (NL) dense_op_nl<R, 1, 2>(v, m, gop, U); else dense_op<R, 1, 2>(v, m, op, U); break;
-    case 2: if (NL) dense_op_nl<R, 2, 1>(v, m, gop, U); else dense_op<R, 2, 1>(v, m, op, U); break;
-    case 3:
-      if (NL) dense_op_nl<R, 3, sizeof(R) == 4 ? SV_K3_G : 1>(v, m, gop, U);
-      else dense_op<R, 3, sizeof(R) == 4 ? SV_K3_G : 1>(v, m, op, U);
-      break;
-    case 4: dense_op_nl<R, 4, 1>(v, m, gop, U); break;
-    case 5: dense_op_nl<R, 5, 1>(v, m, gop, U); break;
-    default: dense_op_nl<R, 6, 1>(v, m, gop, U); break;
+    case 1: dense_op<R, 1, 2>(v, m, op, U); break;
+    case 2: dense_op<R, 2, 1>(v, m, op, U); break;
+    case 3: dense_op<R, 3, sizeof(R) == 4 ? 2 : 1>(v, m, op, U); break;
+    case 4: dense_op_big<R, 4>(v, m, gop, U); break;
+    case 5: dense_op_big<R, 5>(v, m, gop, U); break;
+    default: dense_op_big<R, 6>(v, m, gop, U); break;
   }
 }
 
@@ -475,8 +466,15 @@ __global__ void __launch_bounds__(kTilePassThreads, kTilePassMinBlocks) k_tile(c
 // stops storing tiles, waits (bounded) for its own copies and MMAs, frees
 // its TMEM and returns.
 // ---------------------------------------------------------------------------
-constexpr int kTcThreads = 256;   // two warps per TMEM lane quadrant
+constexpr int kTcThreads = 128;   // thread t <-> TMEM lane (row) t
 constexpr uint32_t kTcSpin = 1u << 22;
+// BF16 operands: one B buffer, 48 KB of shared memory and 128 TMEM columns
+// per CTA, four CTAs per SM; TF32: two B buffers, 96 KB and 256 columns,
+// two CTAs per SM (TMEM admits no more)
+__host__ __device__ constexpr uint32_t tc_bufs(sv_prec mode) {
+  return mode == SV_PREC_TC_TF32X3 ? 2u : 1u;
+}
+constexpr int kTcMinBlocks = 4;
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
@@ -533,53 +531,46 @@ __device__ __forceinline__ int next_tc_op(const TilePass &P, int oi) {
   return -1;
 }
 
-// 16-byte units of tile `tile` <-> the swizzled shared-memory tile (one vector)
-template <bool STORE>
-__device__ __forceinline__ void tc_tile_io(const TilePass &P, uint64_t tile, float2 *v) {
-  const uint32_t nunits = (1u << P.m) / 2;
+// 16-byte units of a 12-qubit tile (one vector) <-> registers / the swizzled
+// shared-memory tile (all of a thread's loads in flight at once).
+constexpr int kTcUnits = (1 << kTcTileM) / 2 / kTcThreads;
+
+__device__ __forceinline__ uint64_t tc_unit(const TilePass &P, uint64_t gthr, int j) {
+  const uint32_t lt = (uint32_t)j * kTcThreads * 2;
   const uint32_t segmask = (1u << P.L) - 1;
-  float2 *g0 = reinterpret_cast<float2 *>(P.v0);
-  const uint64_t base = tile_base(P, tile);
+  return gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
+}
+__device__ __forceinline__ uint64_t tc_thread_base(const TilePass &P, uint64_t tile) {
+  const uint32_t segmask = (1u << P.L) - 1;
   const uint32_t lthr = threadIdx.x * 2;
-  const uint64_t gthr = base | (lthr & segmask) | spread_hi(P, lthr & ~segmask);
-  const uint32_t tstep = blockDim.x * 2;
-  constexpr int BATCH = 8;
-  for (uint32_t i0 = 0; i0 * blockDim.x < nunits; i0 += BATCH) {
-    int4 r[BATCH];
-    uint64_t g[BATCH];
+  return tile_base(P, tile) | (lthr & segmask) | spread_hi(P, lthr & ~segmask);
+}
+__device__ __forceinline__ void tc_load_regs(const TilePass &P, uint64_t tile, int4 (&r)[kTcUnits]) {
+  const float2 *g0 = reinterpret_cast<const float2 *>(P.v0);
+  const uint64_t gthr = tc_thread_base(P, tile);
 #pragma unroll
-    for (int j = 0; j < BATCH; j++) {
-      const uint32_t lt = (i0 + j) * tstep;
-      g[j] = gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
-    }
-    if constexpr (STORE) {
+  for (int j = 0; j < kTcUnits; j++) r[j] = __ldcs(reinterpret_cast<const int4 *>(&g0[tc_unit(P, gthr, j)]));
+}
+__device__ __forceinline__ void tc_put_regs(float2 *v, const int4 (&r)[kTcUnits]) {
 #pragma unroll
-      for (int j = 0; j < BATCH; j++) {
-        const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
-        if (u < nunits) __stcs(reinterpret_cast<int4 *>(&g0[g[j]]), Unit<float>::get(v, u * 2));
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < BATCH; j++) {
-        const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
-        if (u < nunits) r[j] = __ldcs(reinterpret_cast<const int4 *>(&g0[g[j]]));
-      }
-#pragma unroll
-      for (int j = 0; j < BATCH; j++) {
-        const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
-        if (u < nunits) Unit<float>::put(v, u * 2, r[j]);
-      }
-    }
-  }
+  for (int j = 0; j < kTcUnits; j++) Unit<float>::put(v, (j * kTcThreads + threadIdx.x) * 2, r[j]);
+}
+__device__ __forceinline__ void tc_store(const TilePass &P, uint64_t tile, const float2 *v) {
+  float2 *g0 = reinterpret_cast<float2 *>(P.v0);
+  const uint64_t gthr = tc_thread_base(P, tile);
+#pragma unroll 2
+  for (int j = 0; j < kTcUnits; j++)
+    __stcs(reinterpret_cast<int4 *>(&g0[tc_unit(P, gthr, j)]), Unit<float>::get(v, (j * kTcThreads + threadIdx.x) * 2));
 }
 
 struct TcCta {
   uint32_t tmem;       // TMEM base (lane 0, first allocated column)
-  uint32_t bufs;       // shared address of the two B buffers
+  uint32_t bufs;       // shared address of the B buffers
   uint32_t bar_b;      // two mbarriers: B buffer 0 / 1 loaded
   uint32_t bar_mma;    // mbarrier: the op's MMAs completed
   uint32_t *flag;      // shared: the last wait succeeded
   bool tf32;
+  uint32_t nbufs;      // B buffers (1 or 2)
   uint32_t bbytes;     // B hi + lo
   uint32_t a_lo, d;    // TMEM column offsets of A_lo and D (A_hi at 0)
 };
@@ -594,62 +585,61 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 __device__ __forceinline__ bool tc_tile_op(const TilePass &P, const TileOp &op, float2 *v, const TcCta &c,
                                            uint32_t j, int next_op, bool more, uint32_t &pend_b,
                                            uint32_t &pend_mma) {
-  unsigned char *vb = reinterpret_cast<unsigned char *>(v);
-  // warp w serves TMEM lanes (rows) 32 (w % 4) .. + 31 and amplitudes
-  // 16 (w / 4) .. + 15 of each row
-  const int tid = threadIdx.x, warp = tid >> 5, quad = warp & 3, half = warp >> 2;
-  const uint32_t row = 32 * quad + (tid & 31);
-  uint32_t tmask = 0, e[5];
+  const uint32_t vs = smem_u32(v);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint32_t soff[32], tmask = 0;
+  soff[0] = 0;
 #pragma unroll
   for (int q = 0; q < 5; q++) {
     const uint32_t bit = 1u << op.t[q];
     tmask |= bit;
-    e[q] = swb<float>(bit);
+    const uint32_t e = swb<float>(bit);
+#pragma unroll
+    for (int y = 0; y < (1 << q); y++) soff[y + (1 << q)] = soff[y] ^ e;
   }
-  uint32_t soff[16];   // slots of amplitudes 16 half + y, y < 16
-  soff[0] = swb<float>(ins0_mask(row, tmask)) ^ (half ? e[4] : 0u);
+  const uint32_t s0 = swb<float>(ins0_mask((uint32_t)tid, tmask));   // row tid
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  // gather + split, straight into this thread's TMEM lane
 #pragma unroll
-  for (int q = 0; q < 4; q++)
+  for (int h = 0; h < 2; h++) {
+    if (c.tf32) {
 #pragma unroll
-    for (int y = 0; y < (1 << q); y++) soff[y + (1 << q)] = soff[y] ^ e[q];
-  const uint32_t lane_base = (uint32_t)(32 * quad) << 16;
-  // gather + split, straight into the rows' TMEM lanes
-  if (c.tf32) {
+      for (int hh = 0; hh < 2; hh++) {
+        uint32_t hi[16], lo[16];
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
+        for (int y = 0; y < 8; y++) {
+          const float2 a = lds_c(vs + (s0 ^ soff[16 * h + 8 * hh + y]), (const float2 *)nullptr);
+          hi[2 * y] = tf32_hi(a.x);
+          hi[2 * y + 1] = tf32_hi(a.y);
+          lo[2 * y] = __float_as_uint(a.x - __uint_as_float(hi[2 * y]));
+          lo[2 * y + 1] = __float_as_uint(a.y - __uint_as_float(hi[2 * y + 1]));
+        }
+        tmem_st16(c.tmem + lane_base + 32 * h + 16 * hh, hi);
+        tmem_st16(c.tmem + lane_base + c.a_lo + 32 * h + 16 * hh, lo);
+      }
+    } else {
       uint32_t hi[16], lo[16];
 #pragma unroll
-      for (int y = 0; y < 8; y++) {
-        const float2 a = *reinterpret_cast<const float2 *>(vb + soff[8 * h + y]);
-        hi[2 * y] = tf32_hi(a.x);
-        hi[2 * y + 1] = tf32_hi(a.y);
-        lo[2 * y] = __float_as_uint(a.x - __uint_as_float(hi[2 * y]));
-        lo[2 * y + 1] = __float_as_uint(a.y - __uint_as_float(hi[2 * y + 1]));
+      for (int y = 0; y < 16; y++) {
+        const float2 a = lds_c(vs + (s0 ^ soff[16 * h + y]), (const float2 *)nullptr);
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(a.x, a.y);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(a.x - hf.x, a.y - hf.y);
+        hi[y] = *reinterpret_cast<const uint32_t *>(&hb);
+        lo[y] = *reinterpret_cast<const uint32_t *>(&lb);
       }
-      tmem_st16(c.tmem + lane_base + 32 * half + 16 * h, hi);
-      tmem_st16(c.tmem + lane_base + c.a_lo + 32 * half + 16 * h, lo);
+      tmem_st16(c.tmem + lane_base + 16 * h, hi);
+      tmem_st16(c.tmem + lane_base + c.a_lo + 16 * h, lo);
     }
-  } else {
-    uint32_t hi[16], lo[16];
-#pragma unroll
-    for (int y = 0; y < 16; y++) {
-      const float2 a = *reinterpret_cast<const float2 *>(vb + soff[y]);
-      const __nv_bfloat162 hb = __floats2bfloat162_rn(a.x, a.y);
-      const float2 hf = __bfloat1622float2(hb);
-      const __nv_bfloat162 lb = __floats2bfloat162_rn(a.x - hf.x, a.y - hf.y);
-      hi[y] = *reinterpret_cast<const uint32_t *>(&hb);
-      lo[y] = *reinterpret_cast<const uint32_t *>(&lb);
-    }
-    tmem_st16(c.tmem + lane_base + 16 * half, hi);
-    tmem_st16(c.tmem + lane_base + c.a_lo + 16 * half, lo);
   }
   tmem_wait_st();
   tc_fence_before();
   __syncthreads();
   if (tid == 0) {
     tc_fence_after();
-    const uint32_t buf = j & 1;
-    bool ok = mbar_wait(c.bar_b + 8 * buf, (j >> 1) & 1, kTcSpin);
+    // B buffer of op j and the parity of its load's completion
+    const uint32_t nb = c.nbufs, buf = j % nb;
+    bool ok = mbar_wait(c.bar_b + 8 * buf, (j / nb) & 1, kTcSpin);
     if (ok) {
       pend_b = kNone;
       const uint32_t idesc = instr_desc(c.tf32 ? 2u : 1u);
@@ -665,15 +655,22 @@ __device__ __forceinline__ bool tc_tile_op(const TilePass &P, const TileOp &op, 
                        c.bar_mma)
                    : "memory");
       pend_mma = j;
-      // prefetch the next TC op's B into the other buffer (its last reader,
-      // op j - 1, has completed)
-      if (more && next_op >= 0) {
-        const float2 *mats = reinterpret_cast<const float2 *>(P.mats);
-        bulk_load(c.bufs + (buf ^ 1) * c.bbytes, mats + P.ops[next_op].mat, c.bbytes, c.bar_b + 8 * (buf ^ 1));
+      const float2 *mats = reinterpret_cast<const float2 *>(P.mats);
+      const uint32_t nbuf = (j + 1) % nb;
+      // two buffers: prefetch the next TC op's B now (the other buffer's last
+      // reader, op j - 1, has completed); one buffer: once op j's MMAs are done
+      if (nb == 2 && more && next_op >= 0) {
+        bulk_load(c.bufs + nbuf * c.bbytes, mats + P.ops[next_op].mat, c.bbytes, c.bar_b + 8 * nbuf);
         pend_b = j + 1;
       }
       ok = mbar_wait(c.bar_mma, j & 1, kTcSpin);
-      if (ok) pend_mma = kNone;
+      if (ok) {
+        pend_mma = kNone;
+        if (nb == 1 && more && next_op >= 0) {
+          bulk_load(c.bufs, mats + P.ops[next_op].mat, c.bbytes, c.bar_b);
+          pend_b = j + 1;
+        }
+      }
     }
     if (!ok) atomicExch(P.err, 1u);
     *c.flag = ok ? 1u : 0u;
@@ -681,16 +678,19 @@ __device__ __forceinline__ bool tc_tile_op(const TilePass &P, const TileOp &op, 
   __syncthreads();
   if (!*c.flag) return false;
   tc_fence_after();
-  uint32_t r[32];
-  tmem_ld32(c.tmem + lane_base + c.d + 32 * half, r);
 #pragma unroll
-  for (int y = 0; y < 16; y++)
-    *reinterpret_cast<float2 *>(vb + soff[y]) = make_float2(__uint_as_float(r[2 * y]), __uint_as_float(r[2 * y + 1]));
+  for (int h = 0; h < 2; h++) {
+    uint32_t r[32];
+    tmem_ld32(c.tmem + lane_base + c.d + 32 * h, r);
+#pragma unroll
+    for (int y = 0; y < 16; y++)
+      sts_c(vs + (s0 ^ soff[16 * h + y]), make_float2(__uint_as_float(r[2 * y]), __uint_as_float(r[2 * y + 1])));
+  }
   tc_fence_before();
   return true;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 3) k_tile_tc(const __grid_constant__ TilePass P) {
+__global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_tile_tc(const __grid_constant__ TilePass P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t TS = 1u << P.m;
   float2 *tile = reinterpret_cast<float2 *>(smem_raw);
@@ -700,8 +700,9 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tile_tc(const __grid_constant
   c.a_lo = c.tf32 ? 64 : 32;
   c.d = c.tf32 ? 128 : 64;
   const uint32_t ncols = c.tf32 ? 256 : 128;
+  c.nbufs = tc_bufs((sv_prec)((P.flags >> 9) & 3));
   c.bufs = smem_u32(smem_raw) + TS * (uint32_t)sizeof(float2);
-  c.bar_b = c.bufs + 2 * c.bbytes;
+  c.bar_b = c.bufs + c.nbufs * c.bbytes;
   c.bar_mma = c.bar_b + 16;
   uint32_t *slots = reinterpret_cast<uint32_t *>(smem_raw + (c.bar_mma + 8 - smem_u32(smem_raw)));
   c.flag = slots + 1;
@@ -732,7 +733,11 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tile_tc(const __grid_constant
   uint32_t j = 0;   // TC ops done by this CTA
   bool failed = false;
   for (uint64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-    tc_tile_io<false>(P, t, tile);
+    {
+      int4 r[kTcUnits];
+      tc_load_regs(P, t, r);
+      tc_put_regs(tile, r);
+    }
     const uint64_t base = tile_base(P, t);
     const bool more_tiles = t + gridDim.x < ntiles;
     for (int oi = 0; oi < P.nops && !failed; oi++) {
@@ -745,16 +750,18 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tile_tc(const __grid_constant
         j++;
       } else {
         const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);
-        if ((base & gcm) == gcm) apply_op<float, true>(tile, P.m, op, P.ops + oi, mats + op.mat);
+        if ((base & gcm) == gcm) apply_op<float>(tile, P.m, op, P.ops + oi, mats + op.mat);
       }
     }
     __syncthreads();
-    if (!failed) tc_tile_io<true>(P, t, tile);
+    if (failed) break;
+    tc_store(P, t, tile);
+    __syncthreads();   // every thread has read the tile: it may be overwritten
   }
   // no copy or MMA may outlive the CTA
   if (threadIdx.x == 0) {
     if (pend_mma != kNone) mbar_wait(c.bar_mma, pend_mma & 1, kTcSpin);
-    if (pend_b != kNone) mbar_wait(c.bar_b + 8 * (pend_b & 1), (pend_b >> 1) & 1, kTcSpin);
+    if (pend_b != kNone) mbar_wait(c.bar_b + 8 * (pend_b % c.nbufs), (pend_b / c.nbufs) & 1, kTcSpin);
   }
   tc_fence_before();
   __syncthreads();
@@ -765,7 +772,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_tile_tc(const __grid_constant
 
 size_t tc_tile_smem(sv_prec mode) {
   const size_t bbytes = 2 * 64 * 64 * (mode == SV_PREC_TC_TF32X3 ? 4 : 2);
-  return ((size_t)1 << kTcTileM) * 8 + 2 * bbytes + 64;
+  return ((size_t)1 << kTcTileM) * 8 + tc_bufs(mode) * bbytes + 64;
 }
 
 // ---------------------------------------------------------------------------
@@ -879,10 +886,9 @@ sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStr
       SV_CUDA(cudaFuncSetAttribute(k_tile_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
       attr = true;
     }
-    // CTAs per SM: shared memory and TMEM admit three (BF16 operands, 128
-    // TMEM columns each) or two (TF32, 256 columns); the grid strides over the
-    // tiles, so CTAs that do not fit at once simply start later
-    const uint64_t per_sm = mode == SV_PREC_TC_TF32X3 ? 2 : 3;
+    // CTAs per SM as shared memory and TMEM admit them (see tc_bufs); the
+    // grid strides over the tiles, so CTAs that do not fit at once start later
+    const uint64_t per_sm = mode == SV_PREC_TC_TF32X3 ? 2 : (uint64_t)kTcMinBlocks;
     const uint64_t ntiles = 1ull << (p.n - p.m);
     const int grid = (int)std::min<uint64_t>(ntiles, per_sm * (uint64_t)s->sm_count);
     k_tile_tc<<<grid, kTcThreads, smem, stream>>>(p);

@@ -49,9 +49,13 @@ Opts resolve(const sv_state *s, const sv_options *o, int nvec) {
   r.mode = o ? o->mode : SV_MODE_TILED;
   r.fusion_k = std::min(r.fusion_k, 6);
   r.tile_m = std::max(1, std::min(r.tile_m, s->n));
-  // tensor-core blocks run inside the tile passes only when the caller asks
-  // for 12-qubit tiles explicitly; by default they are passes of their own
-  r.tc_in_tile = o && o->tile_m == kTcTileM && r.prec != SV_PREC_PLAIN;
+  // tensor-core blocks run inside 12-qubit tile passes for split-BF16 (four
+  // CTAs per SM fit) unless another tile size is asked for, and for split-TF32
+  // only when 12-qubit tiles are asked for explicitly (its operands admit two
+  // CTAs per SM, and passes of their own measure faster)
+  const bool explicit12 = o && o->tile_m == kTcTileM;
+  const bool default_m = !(o && o->tile_m > 0);
+  r.tc_in_tile = r.prec != SV_PREC_PLAIN && (explicit12 || (r.prec == SV_PREC_TC_BF16X3 && default_m));
   r.L = std::min(r.L, r.tile_m);
   if (s->dt == SV_C64 && r.L < 1) r.L = 1;
   return r;
