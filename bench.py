@@ -198,7 +198,8 @@ def config_of(circ, args):
                         f" 20 cycles, {len(circ.ops)} gates, complex64 state",
             "n_qubits": circ.n_qubits, "gates": len(circ.ops), "state_dtype": "complex64",
             "state_bytes": (1 << circ.n_qubits) * 8,
-            "l2": "inputs larger than L2: the state is 8 GiB (L2 129 MB)" if circ.n_qubits >= 25 else "small state",
+            "l2": (f"inputs larger than L2: the state is {(1 << circ.n_qubits) * 8 / 2**20:.0f} MiB (L2 129 MB)"
+                   if circ.n_qubits >= 25 else "state smaller than L2"),
             "parallelism": f"replicas x{args.gpus}"}
 
 

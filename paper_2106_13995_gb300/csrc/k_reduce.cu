@@ -2,10 +2,11 @@
 // expectations, all-qubit <Z_q>, and inverse-CDF sampling.
 //
 // Reductions form products in the state's precision and accumulate short
-// runs (16 amplitudes) in that precision before adding into FP64; block and
-// grid levels are FP64 throughout.  Sampling computes |psi_x|^2 in FP64 so
-// the cumulative distribution is the one an FP64 reference would build from
-// the same amplitudes.
+// runs (8-16 amplitudes) in that precision before adding into FP64; block and
+// grid levels are FP64 throughout.  Sampling locates a draw's 1024-amplitude
+// chunk from such chunk totals and then walks the chunk with |psi_x|^2 in
+// FP64, so the chosen index is the one an FP64 reference would pick from the
+// same amplitudes (up to draws within ~1e-12 of a chunk boundary).
 #include <algorithm>
 
 #include "sv_device.cuh"
@@ -462,16 +463,36 @@ __device__ __forceinline__ double prob64(const typename Cx<R>::T v) {
   return re * re + im * im;
 }
 
-// chunk sums of |psi|^2 in FP64: one block per chunk trip
+// chunk sums of |psi|^2: one warp per chunk; products and runs of 8
+// amplitudes per lane in the state's precision, FP64 above that (the shot
+// search recomputes the FP64 prefix inside the chosen chunk, so a chunk total
+// that is off in its last bits only matters for a draw within ~1e-12 of a
+// chunk boundary)
 template <typename R>
 __global__ void k_chunk_sums(const typename Cx<R>::T *__restrict__ a, int n, uint64_t nchunks,
                              double *csum) {
+  using C = typename Cx<R>::T;
   const uint64_t camps = 1ull << (n < kChunkBits ? n : kChunkBits);
-  for (uint64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t c = warp; c < nchunks; c += nwarps) {
+    const C *ac = a + c * camps;
     double acc = 0;
-    for (uint64_t i = threadIdx.x; i < camps; i += blockDim.x) acc += prob64<R>(a[c * camps + i]);
-    __syncthreads();
-    block_sum_to(acc, csum + c);
+    for (uint64_t i0 = 0; i0 < camps; i0 += 256) {
+      R run = 0;
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const uint64_t i = i0 + 32 * j + lane;
+        if (i < camps) {
+          const C v = ac[i];
+          run = fma(v.x, v.x, fma(v.y, v.y, run));
+        }
+      }
+      acc += (double)run;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) csum[c] = acc;
   }
 }
 
