@@ -287,7 +287,9 @@ sv_status sv_adjoint_grad_batch(sv_state *const *psi, sv_state *const *lam, int 
  * cached per (n, dtype, op-count bucket, widest op) in memory and, if the
  * SV_TUNE_CACHE environment variable names a file, in that JSON file;
  * sv_apply_circuit and sv_apply_circuit_batch use it for options left at 0.
- * Synchronises. */
+ * Only CUDA-core timings (inout->prec == SV_PREC_PLAIN) enter the cache, and
+ * only calls in that precision mode read it: the tensor-core modes keep
+ * 5-qubit blocks and 12-qubit tiles.  Synchronises. */
 sv_status sv_autotune(sv_state *scratch, const sv_circuit *c, sv_options *inout);
 
 /* Launch a one-thread kernel that waits, bounded by `polls` polls (~128 ns

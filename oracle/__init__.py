@@ -68,6 +68,7 @@ def lib():
             L.or_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
             L.or_splitmix64.restype = C.c_uint64
             L.or_sample.argtypes = [dp, C.c_int, C.c_int64, C.c_uint64, up]
+            L.or_set_num_threads.argtypes = [C.c_int]
             L.or_adjoint_grad.argtypes = [dp, C.c_int, C.POINTER(_OrOp), C.c_int, dp, C.c_int,
                                           up, up, dp, C.c_int, dp, dp]
             _lib = L
@@ -76,6 +77,11 @@ def lib():
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+def set_num_threads(t: int) -> None:
+    """Thread count of later oracle calls (for timing on one core)."""
+    lib().or_set_num_threads(int(t))
 
 
 def _dp(a: np.ndarray):

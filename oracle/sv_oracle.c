@@ -26,6 +26,15 @@ int or_num_threads(void) {
 #endif
 }
 
+/* thread count of later parallel loops (timing on one core vs all cores) */
+void or_set_num_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* gate matrices (the paper names no convention; readings stated per gate)  */
 /* ------------------------------------------------------------------------ */

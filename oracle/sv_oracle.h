@@ -94,6 +94,7 @@ int or_adjoint_grad(double *psi, int n, const or_op *ops, int nops, const double
                     const double *coeff, int nterms, double *expval, double *grad);
 
 int or_num_threads(void);
+void or_set_num_threads(int t);
 
 #ifdef __cplusplus
 }

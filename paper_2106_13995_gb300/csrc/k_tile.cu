@@ -555,12 +555,31 @@ __device__ __forceinline__ void tc_put_regs(float2 *v, const int4 (&r)[kTcUnits]
 #pragma unroll
   for (int j = 0; j < kTcUnits; j++) Unit<float>::put(v, (j * kTcThreads + threadIdx.x) * 2, r[j]);
 }
-__device__ __forceinline__ void tc_store(const TilePass &P, uint64_t tile, const float2 *v) {
+__device__ __forceinline__ void cp_async8(uint32_t smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem), "l"(gmem) : "memory");
+}
+
+// Store the tile; if `next` is a valid tile index, each thread then issues
+// asynchronous copies of its own units of the next tile into the very slots
+// it has just read (no other thread touches them), so the next tile's loads
+// are in flight during the stores and the first op's wait is short.
+__device__ __forceinline__ void tc_store_then_fetch(const TilePass &P, uint64_t tile, float2 *v, bool fetch,
+                                                    uint64_t next) {
   float2 *g0 = reinterpret_cast<float2 *>(P.v0);
   const uint64_t gthr = tc_thread_base(P, tile);
+  const uint64_t gnext = fetch ? tc_thread_base(P, next) : 0;
+  const uint32_t vs = smem_u32(v);
 #pragma unroll 2
-  for (int j = 0; j < kTcUnits; j++)
-    __stcs(reinterpret_cast<int4 *>(&g0[tc_unit(P, gthr, j)]), Unit<float>::get(v, (j * kTcThreads + threadIdx.x) * 2));
+  for (int j = 0; j < kTcUnits; j++) {
+    const uint32_t l = (j * kTcThreads + threadIdx.x) * 2;
+    __stcs(reinterpret_cast<int4 *>(&g0[tc_unit(P, gthr, j)]), Unit<float>::get(v, l));
+    if (fetch) {
+      const float2 *src = &g0[tc_unit(P, gnext, j)];
+      cp_async8(vs + swb<float>(l), src);
+      cp_async8(vs + swb<float>(l + 1), src + 1);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
 struct TcCta {
@@ -733,10 +752,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_tile_tc(const __gr
   uint32_t j = 0;   // TC ops done by this CTA
   bool failed = false;
   for (uint64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-    {
+    if (t == blockIdx.x) {
       int4 r[kTcUnits];
       tc_load_regs(P, t, r);
       tc_put_regs(tile, r);
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this tile's units, fetched during the last store
     }
     const uint64_t base = tile_base(P, t);
     const bool more_tiles = t + gridDim.x < ntiles;
@@ -755,9 +776,9 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_tile_tc(const __gr
     }
     __syncthreads();
     if (failed) break;
-    tc_store(P, t, tile);
-    __syncthreads();   // every thread has read the tile: it may be overwritten
+    tc_store_then_fetch(P, t, tile, more_tiles, t + gridDim.x);
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   // no copy or MMA may outlive the CTA
   if (threadIdx.x == 0) {
     if (pend_mma != kNone) mbar_wait(c.bar_mma, pend_mma & 1, kTcSpin);

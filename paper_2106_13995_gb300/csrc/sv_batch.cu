@@ -66,6 +66,9 @@ static void tune_save_locked() {
 }
 
 void tuned_options(const sv_state *s, const sv_circuit *c, const sv_options *opt, Opts &o) {
+  // the tuner times CUDA-core configurations: tensor-core modes keep their
+  // own defaults (5-qubit blocks, 12-qubit tiles)
+  if (o.prec != SV_PREC_PLAIN) return;
   const bool want_k = !opt || opt->fusion_k == 0, want_m = !opt || opt->tile_m == 0;
   if (!want_k && !want_m) return;
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -317,6 +320,7 @@ sv_status sv_autotune(sv_state *s, const sv_circuit *c, sv_options *inout) {
   cudaEventDestroy(e1);
   inout->fusion_k = bk;
   inout->tile_m = bm;
+  if (inout->prec != SV_PREC_PLAIN) return SV_OK;   // the cache serves CUDA-core defaults only
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_load_locked();
   g_tune[tune_key(s->n, s->dt, c)] = {bk, bm};
