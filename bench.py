@@ -39,7 +39,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "gates/s + HBM GB/s at 30q vs roofline; adjoint grads/s batched vs plain"
 UNIT = "gates/s"
-TILE_KERNEL_SRC = os.path.join(ROOT, "paper_2106_13995_gb300", "csrc", "k_tile.cu")
+TILE_KERNEL_SRC = [os.path.join(ROOT, "paper_2106_13995_gb300", "csrc", f) for f in ("k_tile.cu", "tile_ops.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tile_traffic.json")
 
 
@@ -328,7 +328,7 @@ def main():
         try:
             with open(TRAFFIC_FILE) as f:
                 tr = json.load(f)
-            src_hash = hashlib.sha256(open(TILE_KERNEL_SRC, "rb").read()).hexdigest()[:16]
+            src_hash = hashlib.sha256(b"".join(open(f, "rb").read() for f in TILE_KERNEL_SRC)).hexdigest()[:16]
             if tr.get("k_tile_sha") == src_hash and tr.get("n_qubits") == n:
                 traffic = tr["dram_bytes_per_launch"]
         except Exception:

@@ -293,6 +293,7 @@ size_t sample_shot_offset(int n);
 int64_t sample_shot_capacity();
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch);
 sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream);
+sv_status launch_tile_tc(sv_state *s, const TilePass &p, cudaStream_t stream);   // k_tile_tc.cu
 // tensor-core 5-qubit block (k_tc.cu)
 size_t tc_matrix_words(sv_prec mode);
 void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t> &out);

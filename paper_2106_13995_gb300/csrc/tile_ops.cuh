@@ -1,0 +1,293 @@
+// Tile operations shared by the tile-pass kernels: the swizzled shared-memory
+// layout of a tile, index spreading between tile-local and state indices, and
+// the ops a pass applies to a tile (dense blocks with local controls, diagonal
+// blocks, gradient probes, the 16-byte unit moves of tile loads and stores).
+//
+// Shared-memory layout: amplitude l of the tile lives at sw(l), an XOR
+// swizzle of its low bits by the next bits up.  A gate on low local qubits
+// makes a warp's 32 groups stride through the tile; without the swizzle
+// those strides land on a few banks (up to 8-way conflicts for three low
+// targets), with it every access pattern of the op list spreads over all
+// banks.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "sv_device.cuh"
+#include "sv_internal.h"
+
+namespace sv {
+
+// swizzled shared-memory slot of tile amplitude l (a bijection on [0, 2^m))
+template <typename R> __device__ __forceinline__ uint32_t sw(uint32_t l);
+template <> __device__ __forceinline__ uint32_t sw<float>(uint32_t l) { return l ^ ((l >> 4) & 15u); }
+template <> __device__ __forceinline__ uint32_t sw<double>(uint32_t l) { return l ^ ((l >> 3) & 7u); }
+
+// byte offset of tile amplitude l in the swizzled layout.  The swizzle is
+// linear over GF(2), so swb(a ^ b) = swb(a) ^ swb(b): the offset of a group
+// member is the group base's offset XOR a per-op constant.
+template <typename R> __device__ __forceinline__ uint32_t swb(uint32_t l) {
+  return sw<R>(l) * (uint32_t)sizeof(typename Cx<R>::T);
+}
+
+// shared-memory access by 32-bit address (the tile's slots)
+__device__ __forceinline__ float2 lds_c(uint32_t a, const float2 *) {
+  float2 r;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(r.x), "=f"(r.y) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ double2 lds_c(uint32_t a, const double2 *) {
+  double2 r;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(r.x), "=d"(r.y) : "r"(a));
+  return r;
+}
+__device__ __forceinline__ void sts_c(uint32_t a, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts_c(uint32_t a, double2 v) {
+  asm volatile("st.shared.v2.f64 [%0], {%1, %2};\n" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+
+// State index of tile t's amplitude 0 and of local bits above the L
+// contiguous qubits; only set bits cost work.
+__device__ __forceinline__ uint64_t tile_base(const TilePass &P, uint64_t t) {
+  uint64_t base = 0;
+  for (; t; t &= t - 1) base |= 1ull << P.out_pos[__ffsll((long long)t) - 1];
+  return base;
+}
+
+__device__ __forceinline__ uint64_t spread_hi(const TilePass &P, uint32_t l) {
+  uint64_t g = 0;
+  for (uint32_t x = l >> P.L; x; x &= x - 1) g |= 1ull << P.hi_pos[__ffs(x) - 1];
+  return g;
+}
+
+// two consecutive complex entries of a matrix row (16-byte aligned for c64)
+__device__ __forceinline__ void ld_pair(const float2 *p, float2 &a, float2 &b) {
+  const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+  a = make_float2(q.x, q.y);
+  b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void ld_pair(const double2 *p, double2 &a, double2 &b) {
+  a = __ldg(p);
+  b = __ldg(p + 1);
+}
+
+// Dense block on K local targets (U row-major complex in global memory,
+// read through L1).  Group g's members sit at swb(base(g)) ^ soff[y]; with a
+// power-of-two block size the thread's part of base(g) is computed once per
+// op and each trip adds a warp-uniform part.  Matrices of 1-2 qubits stay in
+// registers for the whole op; larger ones are read per row, each 16-byte load
+// serving G groups.
+template <typename R, int K, int G>
+__device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
+                                         const typename Cx<R>::T *__restrict__ U) {
+  using C = typename Cx<R>::T;
+  constexpr int D = 1 << K;
+  constexpr bool kRegU = K <= 2;
+  constexpr bool kUnrollRows = K <= 3;
+  const uint32_t vs = smem_u32(v);
+  uint32_t soff[D], e[K], tmask = 0;
+  soff[0] = 0;
+#pragma unroll
+  for (int j = 0; j < K; j++) {
+    const uint32_t bit = 1u << op.t[j];
+    tmask |= bit;
+    e[j] = swb<R>(bit);
+#pragma unroll
+    for (int y = 0; y < (1 << j); y++) soff[y + (1 << j)] = soff[y] ^ e[j];
+  }
+  C ur[kRegU ? D * D : 1];
+  if constexpr (kRegU) {
+#pragma unroll
+    for (int q = 0; q < D * D; q += 2) ld_pair(U + q, ur[q], ur[q + 1]);
+  }
+  const uint32_t fixed = tmask | op.lcmask;
+  const uint32_t ngroups = 1u << (m - __popc(fixed));
+  const uint32_t T = blockDim.x;
+  if (threadIdx.x >= ngroups) return;
+  // thread t's groups are t + c T, c < ntrips; base(t + c T) = base(t) ^ D(c)
+  // with D linear in c: D(c) = XOR of f[j] over the set bits j of c
+  const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
+  const uint32_t sthr = swb<R>(ins0_mask(threadIdx.x, fixed) | op.lcmask);
+  for (uint32_t c0 = 0; c0 < ntrips; c0 += G) {
+    uint32_t s[G];
+    bool ok[G];
+    C x[G][D];
+#pragma unroll
+    for (int h = 0; h < G; h++) {
+      const uint32_t cc = c0 + h;
+      ok[h] = cc < ntrips;
+      s[h] = sthr ^ swb<R>(ins0_mask(ok[h] ? cc * T : 0u, fixed));
+#pragma unroll
+      for (int y = 0; y < D; y++) {
+        x[h][y] = lds_c(vs + (s[h] ^ soff[y]), (const C *)nullptr);
+      }
+    }
+#pragma unroll(kUnrollRows ? D : 1)
+    for (int r = 0; r < D; r++) {
+      C a[G];
+#pragma unroll
+      for (int h = 0; h < G; h++) a[h] = czero<C>();
+#pragma unroll
+      for (int y = 0; y < D; y += 2) {
+        C u0, u1;
+        if constexpr (kRegU) {
+          u0 = ur[(r * D + y) % (kRegU ? D * D : 1)];
+          u1 = ur[(r * D + y + 1) % (kRegU ? D * D : 1)];
+        } else {
+          ld_pair(U + r * D + y, u0, u1);
+        }
+#pragma unroll
+        for (int h = 0; h < G; h++) {
+          a[h] = cfma(u0, x[h][y], a[h]);
+          a[h] = cfma(u1, x[h][y + 1], a[h]);
+        }
+      }
+      uint32_t so;
+      if constexpr (kUnrollRows) {
+        so = soff[r % D];
+      } else {
+        so = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++) so ^= ((r >> j) & 1) ? e[j] : 0u;
+      }
+#pragma unroll
+      for (int h = 0; h < G; h++)
+        if (ok[h]) {
+          sts_c(vs + (s[h] ^ so), a[h]);
+        }
+    }
+  }
+}
+
+// Dense blocks of 4..6 qubits keep 2^k amplitudes per thread; they run as
+// functions of their own so their registers do not crowd the k <= 3 paths
+// that make up most passes.  The op is read from global memory here, so no
+// caller keeps an addressable (local-memory) copy of it.
+template <typename R, int K>
+__device__ __noinline__ void dense_op_big(typename Cx<R>::T *__restrict__ v, int m, const TileOp *gop,
+                                          const typename Cx<R>::T *__restrict__ U) {
+  const TileOp op = *gop;
+  dense_op<R, K, 1>(v, m, op, U);
+}
+
+// Diagonal block: amplitude l is multiplied by d[r(l)], r(l) the target bits
+// of l.  Both the slot and r are linear in l, so each splits into a thread
+// part and a warp-uniform trip part.
+template <typename R>
+__device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
+                                        const typename Cx<R>::T *__restrict__ d) {
+  using C = typename Cx<R>::T;
+  unsigned char *vb = reinterpret_cast<unsigned char *>(v);
+  const uint32_t ngroups = 1u << (m - __popc(op.lcmask));
+  const uint32_t T = blockDim.x;
+  if (threadIdx.x >= ngroups) return;
+  uint32_t tpos[6];
+#pragma unroll
+  for (int j = 0; j < 6; j++) tpos[j] = op.t[j];
+  const int k = op.k;
+  auto rows = [&](uint32_t l) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int j = 0; j < 6; j++)
+      if (j < k) r |= ((l >> tpos[j]) & 1u) << j;
+    return r;
+  };
+  const uint32_t lthr = ins0_mask(threadIdx.x, op.lcmask) | op.lcmask;
+  const uint32_t sthr = swb<R>(lthr), rthr = rows(lthr);
+  for (uint32_t g0 = 0; g0 < ngroups; g0 += T) {
+    const uint32_t lg = ins0_mask(g0, op.lcmask);
+    C *p = reinterpret_cast<C *>(vb + (sthr ^ swb<R>(lg)));
+    *p = cmul(__ldg(&d[rthr ^ rows(lg)]), *p);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const TileOp &op, const TileOp *gop,
+                                         const typename Cx<R>::T *U) {
+  if (op.kind == TOP_DIAG) {
+    diag_op<R>(v, m, op, U);
+    return;
+  }
+  switch (op.k) {
+    case 1: dense_op<R, 1, 2>(v, m, op, U); break;
+    case 2: dense_op<R, 2, 1>(v, m, op, U); break;
+    case 3: dense_op<R, 3, sizeof(R) == 4 ? 2 : 1>(v, m, op, U); break;
+    case 4: dense_op_big<R, 4>(v, m, gop, U); break;
+    case 5: dense_op_big<R, 5>(v, m, gop, U); break;
+    default: dense_op_big<R, 6>(v, m, gop, U); break;
+  }
+}
+
+// Im(conj(b) a)
+template <typename C> __device__ __forceinline__ auto imdot(C b, C a) -> decltype(a.x) {
+  return b.x * a.y - b.y * a.x;
+}
+
+template <typename R>
+__device__ __forceinline__ void block_acc(R part, double *dst) {
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) atomicAdd(dst, (double)part);
+}
+
+template <typename R>
+__device__ void grad_op(const typename Cx<R>::T *__restrict__ psi,
+                        const typename Cx<R>::T *__restrict__ lam, int m, const TileOp &op,
+                        double *acc) {
+  using C = typename Cx<R>::T;
+  const int t = op.t[0];
+  const uint32_t bit = 1u << t;
+  const uint32_t ngroups = 1u << (m - 1);
+  R part = 0;
+  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const uint32_t l0 = ins0(g, t), l1 = l0 | bit;
+    const uint32_t p0 = sw<R>(l0), p1 = sw<R>(l1);
+    const C a0 = psi[p0], a1 = psi[p1], b0 = lam[p0], b1 = lam[p1];
+    switch (op.gen) {
+      case 1:  // X
+        part += imdot(b0, a1) + imdot(b1, a0);
+        break;
+      case 2: {  // Y: (Y psi)[l0] = -i a1, (Y psi)[l1] = i a0
+        C ma1 = cmake(a1.y, -a1.x), pa0 = cmake(-a0.y, a0.x);
+        part += imdot(b0, ma1) + imdot(b1, pa0);
+        break;
+      }
+      case 3:  // Z
+        part += imdot(b0, a0) - imdot(b1, a1);
+        break;
+      default:  // diag(0, -2)
+        part += R(-2) * imdot(b1, a1);
+        break;
+    }
+  }
+  block_acc<R>(part, acc + op.slot);
+}
+
+// 16-byte unit u of the tile <-> shared memory (swizzled amplitude slots)
+template <typename R> struct Unit;
+template <> struct Unit<float> {
+  static constexpr uint32_t APU = 2;
+  __device__ static void put(float2 *v, uint32_t l, int4 raw) {
+    const float4 f = *reinterpret_cast<const float4 *>(&raw);
+    v[sw<float>(l)] = make_float2(f.x, f.y);
+    v[sw<float>(l + 1)] = make_float2(f.z, f.w);
+  }
+  __device__ static int4 get(const float2 *v, uint32_t l) {
+    const float2 a = v[sw<float>(l)], b = v[sw<float>(l + 1)];
+    const float4 f = make_float4(a.x, a.y, b.x, b.y);
+    return *reinterpret_cast<const int4 *>(&f);
+  }
+};
+template <> struct Unit<double> {
+  static constexpr uint32_t APU = 1;
+  __device__ static void put(double2 *v, uint32_t l, int4 raw) {
+    v[sw<double>(l)] = *reinterpret_cast<const double2 *>(&raw);
+  }
+  __device__ static int4 get(const double2 *v, uint32_t l) {
+    const double2 a = v[sw<double>(l)];
+    return *reinterpret_cast<const int4 *>(&a);
+  }
+};
+
+}  // namespace sv
