@@ -148,6 +148,31 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle on host cores (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
+def pin_to_gpu_numa_node():
+    """Restrict this process to the CPUs of the GPU's NUMA node (read from
+    sysfs through the PCI bus id nvidia-smi reports), so host buffers it
+    allocates and touches next are local to the GPU.  Returns the node, or
+    None when the topology is not available."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i",
+                              os.environ.get("LOCAL_RANK", "0")], capture_output=True, text=True,
+                             timeout=20).stdout.strip().splitlines()[0].strip()
+        dom, rest = bus.split(":", 1)
+        dev = f"{int(dom, 16):04x}:{rest.lower()}"
+        node = int(open(f"/sys/bus/pci/devices/{dev}/numa_node").read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        if cpus:
+            os.sched_setaffinity(0, cpus)
+        return node
+    except Exception:
+        return None
+
+
 def oracle_sample(circ, budget_s: float, max_gates=None):
     """Apply the circuit's gates one by one with the FP64 oracle to a 2^n
     complex128 state until the time budget is spent.  Returns (gates/s,
@@ -288,7 +313,10 @@ def main():
 
     # ---- end to end through the C ABI from host buffers -----------------------
     if "e2e" in sections:
+        aff = os.sched_getaffinity(0)
+        numa = pin_to_gpu_numa_node()   # pinned pages land on the GPU's NUMA node
         host = torch.zeros(2 << n, dtype=torch.float32, pin_memory=True)
+        os.sched_setaffinity(0, aff)
         host[0] = 1.0
         hp = host.data_ptr()
 
@@ -313,7 +341,8 @@ def main():
         tu = timed(upload_only, 2) / 2
         out["e2e"] = {"value": len(circ.ops) * ke * world / te, "unit": UNIT,
                       "h2d_bytes_per_step": state.nbytes, "d2h_bytes_per_step": 8 * n + 8 + 8 * 1000,
-                      "ms_per_step": 1e3 * te / ke, "h2d_gbs": state.nbytes / tu / 1e9}
+                      "ms_per_step": 1e3 * te / ke, "h2d_gbs": state.nbytes / tu / 1e9,
+                      "host_numa_node": numa}
         del host
 
     # ---- roofline of the dominant kernel (the tile pass) -----------------------

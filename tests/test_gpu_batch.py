@@ -128,3 +128,36 @@ def test_batch_timeout_reports_status(svlib):
     for c, s in zip(circs, states):
         ref = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c).numpy()
         assert np.array_equal(s.numpy(), ref)
+
+
+def test_autotune_cache_leaves_tensor_core_modes_alone(svlib, oracle):
+    """A CUDA-core tuning in the cache must not change what a tensor-core
+    mode plans: the BF16 mode still fuses 5-qubit blocks (the block count of
+    an explicit fusion width of 5) and its result differs from the CUDA-core
+    one only by split-BF16 rounding."""
+    from paper_2106_13995_gb300 import _native as N
+    c = W.random_u3_cz(16, 12, 9)
+    m = svlib.marshal(c)
+    s = svlib.StateVector(16, "c64")
+    o = svlib.options()
+    N.check(N.lib().sv_autotune(s.h, m.ref(), C.byref(o)))
+    tc = svlib.options(prec=N.SV_PREC_TC_BF16X3)
+    nb_tc, _ = s.plan_info(m, opts=tc)
+    nb_k5, _ = s.plan_info(m, opts=svlib.options(fusion_k=5))
+    assert nb_tc == nb_k5, (nb_tc, nb_k5, o.fusion_k)
+    a = s.set_basis(0).apply_circuit(m).numpy()
+    b = s.set_basis(0).apply_circuit(m, opts=tc).numpy()
+    assert not np.array_equal(a, b)
+    inf, _ = fidelity_metrics(oracle.run(c), b)
+    assert inf <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_uneven_circuits_tensor_core_modes(svlib, oracle, prec):
+    """Per-circuit tensor-core modes on uneven widths (12..16 qubits) against
+    the FP64 oracle."""
+    circs = small_uneven(6, 12, 16, 12, seed=11)
+    for c in circs:
+        s = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c, opts=svlib.options(prec=prec))
+        inf, _ = fidelity_metrics(oracle.run(c), s.numpy())
+        assert inf <= 1e-5, (c.name, prec, inf)
