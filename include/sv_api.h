@@ -60,10 +60,12 @@ typedef enum {
 typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
 
 /* Arithmetic of fused dense blocks.  In the tensor-core modes the fusion
- * width defaults to 5 and every dense 5-qubit block is applied on the tensor
- * cores (complex64 states of >= 12 qubits): as a pass of its own by default,
- * or inside 12-qubit tile passes when sv_options.tile_m is set to 12.
- * complex128 states always use FP64 CUDA-core arithmetic. */
+ * width defaults to 5 and every dense 4- or 5-qubit block is applied on the
+ * tensor cores (complex64 states of >= 12 qubits; a 4-qubit block is padded
+ * with an idle qubit).  Split-BF16 runs them inside 12-qubit tile passes
+ * unless sv_options.tile_m asks for another tile size; split-TF32 runs them
+ * as passes of their own unless tile_m is 12.  complex128 states always use
+ * FP64 CUDA-core arithmetic. */
 typedef enum {
   SV_PREC_PLAIN = 0,       /* FP32 FMA on CUDA cores */
   SV_PREC_TC_BF16X3 = 1,   /* tensor cores, split-BF16 (3 products), FP32 accumulate */
