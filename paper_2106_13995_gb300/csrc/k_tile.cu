@@ -19,10 +19,17 @@
 namespace sv {
 
 constexpr int kTileMaxThreads = 512;    // persistent batch kernel
-// tile passes: at most 256 threads (larger tiles give each thread more
-// amplitudes), four CTAs per SM (64 registers a thread)
+// tile passes: 32 amplitudes per thread (each op's set-up is paid for that
+// many), at most 256 threads, up to 80 registers a thread
 constexpr int kTilePassThreads = 256;
-constexpr int kTilePassMinBlocks = 4;
+constexpr int kTilePassMinBlocks = 3;
+
+__device__ __forceinline__ void cp_async8(uint32_t smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem), "l"(gmem) : "memory");
+}
 
 // The work of one CTA on one tile.  COH selects L2-coherent loads and stores
 // (bypassing L1), needed when other CTAs of the same launch wrote the tile
@@ -51,29 +58,49 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
     const uint32_t lt = i * tstep;     // bits above the thread bits
     return gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
   };
-  // loads: four 16-byte units in flight per thread before any shared store
-  constexpr int BATCH = 4;
-  for (uint32_t i0 = 0; i0 * blockDim.x + threadIdx.x < nunits; i0 += BATCH) {
-    int4 r0[BATCH], r1[BATCH];
-#pragma unroll
-    for (int j = 0; j < BATCH; j++) {
-      const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
-      if (u < nunits) {
-        const uint64_t g = goff(i0 + j);
-        const int4 *p0 = reinterpret_cast<const int4 *>(&g0[g]);
-        r0[j] = COH ? __ldcg(p0) : __ldcs(p0);
+  if constexpr (!COH) {
+    // loads: asynchronous copies straight into the swizzled slots (8 bytes
+    // per complex64 amplitude: a unit's two slots may be swapped), all of a
+    // thread's copies in flight at once
+    const uint32_t vs0 = smem_u32(v0), vs1 = smem_u32(v1);
+    for (uint32_t i = 0; i * blockDim.x + threadIdx.x < nunits; i++) {
+      const uint64_t g = goff(i);
+      const uint32_t l = (i * blockDim.x + threadIdx.x) * UN::APU;
+      if (sizeof(C) == 8) {
+        cp_async8(vs0 + swb<R>(l), &g0[g]);
+        cp_async8(vs0 + swb<R>(l + 1), &g0[g + 1]);
         if (load1) {
-          const int4 *p1 = reinterpret_cast<const int4 *>(&g1[g]);
-          r1[j] = COH ? __ldcg(p1) : __ldcs(p1);
+          cp_async8(vs1 + swb<R>(l), &g1[g]);
+          cp_async8(vs1 + swb<R>(l + 1), &g1[g + 1]);
         }
+      } else {
+        cp_async16(vs0 + swb<R>(l), &g0[g]);
+        if (load1) cp_async16(vs1 + swb<R>(l), &g1[g]);
       }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  } else {
+    // loads through L2 only (other CTAs of the launch wrote the tile): four
+    // 16-byte units in flight per thread before any shared store
+    constexpr int BATCH = 4;
+    for (uint32_t i0 = 0; i0 * blockDim.x + threadIdx.x < nunits; i0 += BATCH) {
+      int4 r0[BATCH], r1[BATCH];
 #pragma unroll
-    for (int j = 0; j < BATCH; j++) {
-      const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
-      if (u < nunits) {
-        UN::put(v0, u * UN::APU, r0[j]);
-        if (load1) UN::put(v1, u * UN::APU, r1[j]);
+      for (int j = 0; j < BATCH; j++) {
+        const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
+        if (u < nunits) {
+          const uint64_t g = goff(i0 + j);
+          r0[j] = __ldcg(reinterpret_cast<const int4 *>(&g0[g]));
+          if (load1) r1[j] = __ldcg(reinterpret_cast<const int4 *>(&g1[g]));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < BATCH; j++) {
+        const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
+        if (u < nunits) {
+          UN::put(v0, u * UN::APU, r0[j]);
+          if (load1) UN::put(v1, u * UN::APU, r1[j]);
+        }
       }
     }
   }
@@ -244,7 +271,7 @@ __global__ void k_wait_selftest(const uint32_t *never, uint32_t *err, uint64_t l
 
 int tile_threads(int m, sv_dtype dt) {
   const int units = (1 << m) / (dt == SV_C64 ? 2 : 1);
-  int t = units / 8;
+  int t = units / 16;
   if (t < 32) t = 32;
   if (t > kTilePassThreads) t = kTilePassThreads;
   return t;

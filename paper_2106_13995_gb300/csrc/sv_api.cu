@@ -43,7 +43,12 @@ size_t red_bytes(int n) {
 Opts resolve(const sv_state *s, const sv_options *o, int nvec) {
   Opts r;
   r.fusion_k = (o && o->fusion_k > 0) ? o->fusion_k : (o && o->prec != SV_PREC_PLAIN ? 5 : 3);
-  r.tile_m = (o && o->tile_m > 0) ? o->tile_m : (s->dt == SV_C64 ? 12 : 12) - (nvec - 1);
+  // default tiles: 13 qubits for single-vector CUDA-core passes on complex64
+  // (fewer passes; 32 amplitudes per thread at 256 threads), 12 otherwise
+  // (tensor-core tile passes need 12; two-vector and complex128 tiles would
+  // crowd shared memory)
+  const bool plain64 = s->dt == SV_C64 && nvec == 1 && !(o && o->prec != SV_PREC_PLAIN);
+  r.tile_m = (o && o->tile_m > 0) ? o->tile_m : (plain64 ? 13 : 12 - (nvec - 1));
   r.L = s->dt == SV_C64 ? 4 : 3;
   r.prec = o ? o->prec : SV_PREC_PLAIN;
   r.mode = o ? o->mode : SV_MODE_TILED;

@@ -211,8 +211,10 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
     return;
   }
   switch (op.k) {
-    case 1: dense_op<R, 1, 2>(v, m, op, U); break;
-    case 2: dense_op<R, 2, 1>(v, m, op, U); break;
+    // groups per trip: as many as the registers allow next to a thread's
+    // amplitudes (complex128 needs twice the registers per amplitude)
+    case 1: dense_op<R, 1, sizeof(R) == 4 ? 4 : 2>(v, m, op, U); break;
+    case 2: dense_op<R, 2, sizeof(R) == 4 ? 2 : 1>(v, m, op, U); break;
     case 3: dense_op<R, 3, sizeof(R) == 4 ? 2 : 1>(v, m, op, U); break;
     case 4: dense_op_big<R, 4>(v, m, gop, U); break;
     case 5: dense_op_big<R, 5>(v, m, gop, U); break;
