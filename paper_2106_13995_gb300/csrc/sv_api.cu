@@ -105,6 +105,47 @@ template <typename R> static void put_c(std::vector<uint8_t> &pool, cd v) {
   pool.insert(pool.end(), p, p + sizeof(t));
 }
 
+// Positions of a tile op's thread-index bits.  The groups of an op are the
+// local indices with zeros at its fixed positions (targets, local controls);
+// thread bit i takes the i-th lowest free position, except that lane bit j
+// (j < NB) takes position j or j + NB when one of them is among the first
+// log2(T) free positions: the swizzle folds both onto slot bit j, so the
+// 2^NB lanes of one shared-memory wavefront reach different bank rows.  Only
+// the first log2(T) positions are permuted (T = the fewest threads a pass of
+// this tile size runs with), so larger blocks keep the same trip positions.
+static void set_thread_positions(TileOp &op, uint32_t fixed, int m, sv_dtype dt) {
+  const int NB = dt == SV_C64 ? 4 : 3;
+  int ntb = 0;
+  while ((1 << (ntb + 1)) <= tile_threads(m, dt)) ntb++;
+  int pos[9], nf = 0;
+  for (int p = 0; p < m && nf < 9; p++)
+    if (!((fixed >> p) & 1u)) pos[nf++] = p;
+  const int nlim = std::min(ntb, nf);
+  int P[9];
+  uint32_t used = 0;
+  for (int i = 0; i < 9; i++) P[i] = -1;
+  for (int j = 0; j < std::min(NB, nlim); j++)
+    for (int c : {j, j + NB}) {
+      bool among = false;
+      for (int i = 0; i < nlim; i++) among |= pos[i] == c;
+      if (among && !((used >> c) & 1u)) {
+        P[j] = c;
+        used |= 1u << c;
+        break;
+      }
+    }
+  int r = 0;
+  for (int i = 0; i < nlim; i++)
+    if (P[i] < 0) {
+      while ((used >> pos[r]) & 1u) r++;
+      P[i] = pos[r];
+      used |= 1u << pos[r];
+    }
+  for (int i = nlim; i < nf; i++) P[i] = pos[i];
+  std::memset(op.tbpos, 0, sizeof(op.tbpos));
+  for (int i = 0; i < nf; i++) op.tbpos[i >> 1] |= (uint8_t)(P[i] << (4 * (i & 1)));
+}
+
 // Convert one planned pass into TilePass + TileOps (+ matrices).
 sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
                            std::vector<uint32_t> &op0s, const std::vector<int> &batch_mat_off) {
@@ -141,6 +182,10 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
     }
     if (blk.kind == TOP_DENSE && blk.diag) op.kind = TOP_DIAG;
     if (op.kind == TOP_DENSE || op.kind == TOP_DIAG) {
+      uint32_t fixed = op.lcmask;
+      if (op.kind == TOP_DENSE)
+        for (int j = 0; j < op.k; j++) fixed |= 1u << op.t[j];
+      set_thread_positions(op, fixed, tp.m, b.dt);
       if (blk.inst >= 0 && !batch_mat_off.empty()) {
         op.gen = kGenBatchMat;
         op.mat = (uint32_t)batch_mat_off[blk.inst];

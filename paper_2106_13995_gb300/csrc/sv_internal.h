@@ -57,7 +57,7 @@ struct TileOp {
   uint8_t vmask;      // bit0: apply to v0, bit1: apply to v1
   uint8_t gen;        // TOP_GRAD generator: 1=X 2=Y 3=Z 4=diag(0,-2)
   uint8_t t[6];       // local target positions, matrix bit order
-  uint8_t ts[6];      // the same positions sorted ascending
+  uint8_t tbpos[6];   // dense/diag: local position of thread-index bit i (4 bits each, i < 9)
   uint32_t lcmask;    // local control mask (bits of the tile-local index)
   uint32_t mat;       // offset (complex entries) into the matrix pool; TOP_PAULI: coeff index
   uint32_t gcmask_lo; // controls outside the tile, as a mask of global bits (low 32)

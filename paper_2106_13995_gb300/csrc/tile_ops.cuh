@@ -62,6 +62,39 @@ __device__ __forceinline__ uint64_t spread_hi(const TilePass &P, uint32_t l) {
   return g;
 }
 
+// Trip part of a group's local index.  A thread's groups are g = t + c T
+// (t < T, T a power of two), and the local index inserts zeros at the op's
+// fixed bit positions: l(g) = l(t) ^ l(c T), both maps linear over GF(2).
+// For l(c T) the fixed positions below the trip bits only shift them up,
+// the same for every c; only fixed positions above need a per-trip insert.
+struct TripMap {
+  uint32_t shift;  // log2(T) + fixed bits below the trip region
+  uint32_t hi;     // fixed bits above it
+};
+__device__ __forceinline__ TripMap trip_map(uint32_t T, uint32_t fixed) {
+  uint32_t low = __ffs(T) - 1, f = fixed;
+  while (f) {
+    const uint32_t p = __ffs(f) - 1;
+    if (p > low) break;
+    f &= f - 1;
+    low++;
+  }
+  return {low, f};
+}
+__device__ __forceinline__ uint32_t trip_l(uint32_t c, const TripMap &tm) {
+  return ins0_mask(c << tm.shift, tm.hi);
+}
+
+// Local index of thread t's first group: thread bit i goes to the position
+// the plan stored for it (the free positions of the op, with the lane bits
+// arranged so that one shared-memory wavefront spans all bank rows).
+__device__ __forceinline__ uint32_t thread_l(uint32_t t, const TileOp &op) {
+  uint32_t l = 0;
+#pragma unroll
+  for (int i = 0; i < 9; i++) l |= ((t >> i) & 1u) << ((op.tbpos[i >> 1] >> (4 * (i & 1))) & 15u);
+  return l;
+}
+
 // two consecutive complex entries of a matrix row (16-byte aligned for c64)
 __device__ __forceinline__ void ld_pair(const float2 *p, float2 &a, float2 &b) {
   const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
@@ -106,19 +139,23 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
   const uint32_t ngroups = 1u << (m - __popc(fixed));
   const uint32_t T = blockDim.x;
   if (threadIdx.x >= ngroups) return;
-  // thread t's groups are t + c T, c < ntrips; base(t + c T) = base(t) ^ D(c)
-  // with D linear in c: D(c) = XOR of f[j] over the set bits j of c
+  // thread t's groups are t + c T, c < ntrips; slot(t + c T) = slot(t) ^
+  // slot(c T), and a trip's G groups c0 + h share slot(c0 T)
   const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
-  const uint32_t sthr = swb<R>(ins0_mask(threadIdx.x, fixed) | op.lcmask);
+  const uint32_t sthr = swb<R>(thread_l(threadIdx.x, op) | op.lcmask);
+  const TripMap tm = trip_map(T, fixed);
+  uint32_t dh[G];
+#pragma unroll
+  for (int h = 0; h < G; h++) dh[h] = swb<R>(trip_l(h, tm));
   for (uint32_t c0 = 0; c0 < ntrips; c0 += G) {
     uint32_t s[G];
     bool ok[G];
     C x[G][D];
+    const uint32_t sc = sthr ^ swb<R>(trip_l(c0, tm));
 #pragma unroll
     for (int h = 0; h < G; h++) {
-      const uint32_t cc = c0 + h;
-      ok[h] = cc < ntrips;
-      s[h] = sthr ^ swb<R>(ins0_mask(ok[h] ? cc * T : 0u, fixed));
+      ok[h] = c0 + h < ntrips;
+      s[h] = ok[h] ? sc ^ dh[h] : sthr;
 #pragma unroll
       for (int y = 0; y < D; y++) {
         x[h][y] = lds_c(vs + (s[h] ^ soff[y]), (const C *)nullptr);
@@ -161,6 +198,108 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
   }
 }
 
+// Packed FP32 pairs: one f32x2 instruction performs two FMAs.
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(uint64_t r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t lds_b64(uint32_t a) {
+  uint64_t r;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(r) : "r"(a));
+  return r;
+}
+
+// complex64 dense block with packed FP32 arithmetic: for output row r the
+// pair (re, im) accumulates Re(u) (x re, x im) and, separately,
+// Im(u) (x re, x im); the two combine into u x once per row.
+template <int K, int G>
+__device__ __forceinline__ void dense_op_f2(float2 *__restrict__ v, int m, const TileOp &op,
+                                            const float2 *__restrict__ U) {
+  constexpr int D = 1 << K;
+  constexpr bool kRegU = K <= 2;
+  const uint32_t vs = smem_u32(v);
+  uint32_t soff[D], tmask = 0;
+  soff[0] = 0;
+#pragma unroll
+  for (int j = 0; j < K; j++) {
+    const uint32_t bit = 1u << op.t[j];
+    tmask |= bit;
+    const uint32_t e = swb<float>(bit);
+#pragma unroll
+    for (int y = 0; y < (1 << j); y++) soff[y + (1 << j)] = soff[y] ^ e;
+  }
+  float2 ur[kRegU ? D * D : 1];
+  if constexpr (kRegU) {
+#pragma unroll
+    for (int q = 0; q < D * D; q += 2) ld_pair(U + q, ur[q], ur[q + 1]);
+  }
+  const uint32_t fixed = tmask | op.lcmask;
+  const uint32_t ngroups = 1u << (m - __popc(fixed));
+  const uint32_t T = blockDim.x;
+  if (threadIdx.x >= ngroups) return;
+  const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
+  const uint32_t sthr = swb<float>(thread_l(threadIdx.x, op) | op.lcmask);
+  const TripMap tm = trip_map(T, fixed);
+  uint32_t dh[G];
+#pragma unroll
+  for (int h = 0; h < G; h++) dh[h] = swb<float>(trip_l(h, tm));
+  for (uint32_t c0 = 0; c0 < ntrips; c0 += G) {
+    uint32_t s[G];
+    bool ok[G];
+    uint64_t x[G][D];
+    const uint32_t sc = sthr ^ swb<float>(trip_l(c0, tm));
+#pragma unroll
+    for (int h = 0; h < G; h++) {
+      ok[h] = c0 + h < ntrips;
+      s[h] = ok[h] ? sc ^ dh[h] : sthr;
+#pragma unroll
+      for (int y = 0; y < D; y++) x[h][y] = lds_b64(vs + (s[h] ^ soff[y]));
+    }
+#pragma unroll
+    for (int r = 0; r < D; r++) {
+      uint64_t a1[G], a2[G];
+#pragma unroll
+      for (int h = 0; h < G; h++) a1[h] = a2[h] = 0ull;
+#pragma unroll
+      for (int y = 0; y < D; y += 2) {
+        float2 u0, u1;
+        if constexpr (kRegU) {
+          u0 = ur[(r * D + y) % (kRegU ? D * D : 1)];
+          u1 = ur[(r * D + y + 1) % (kRegU ? D * D : 1)];
+        } else {
+          ld_pair(U + r * D + y, u0, u1);
+        }
+        const uint64_t r0 = pk2(u0.x, u0.x), i0 = pk2(u0.y, u0.y);
+        const uint64_t r1 = pk2(u1.x, u1.x), i1 = pk2(u1.y, u1.y);
+#pragma unroll
+        for (int h = 0; h < G; h++) {
+          a1[h] = fma2(r0, x[h][y], a1[h]);
+          a2[h] = fma2(i0, x[h][y], a2[h]);
+          a1[h] = fma2(r1, x[h][y + 1], a1[h]);
+          a2[h] = fma2(i1, x[h][y + 1], a2[h]);
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < G; h++)
+        if (ok[h]) {
+          const float2 p = upk2(a1[h]), q = upk2(a2[h]);
+          sts_c(vs + (s[h] ^ soff[r]), make_float2(p.x - q.y, p.y + q.x));
+        }
+    }
+  }
+}
+
 // Dense blocks of 4..6 qubits keep 2^k amplitudes per thread; they run as
 // functions of their own so their registers do not crowd the k <= 3 paths
 // that make up most passes.  The op is read from global memory here, so no
@@ -194,10 +333,11 @@ __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m
       if (j < k) r |= ((l >> tpos[j]) & 1u) << j;
     return r;
   };
-  const uint32_t lthr = ins0_mask(threadIdx.x, op.lcmask) | op.lcmask;
+  const uint32_t lthr = thread_l(threadIdx.x, op) | op.lcmask;
   const uint32_t sthr = swb<R>(lthr), rthr = rows(lthr);
-  for (uint32_t g0 = 0; g0 < ngroups; g0 += T) {
-    const uint32_t lg = ins0_mask(g0, op.lcmask);
+  const TripMap tm = trip_map(T, op.lcmask);
+  for (uint32_t g0 = 0, c = 0; g0 < ngroups; g0 += T, c++) {
+    const uint32_t lg = trip_l(c, tm);
     C *p = reinterpret_cast<C *>(vb + (sthr ^ swb<R>(lg)));
     *p = cmul(__ldg(&d[rthr ^ rows(lg)]), *p);
   }
@@ -209,6 +349,14 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
   if (op.kind == TOP_DIAG) {
     diag_op<R>(v, m, op, U);
     return;
+  }
+  if constexpr (sizeof(R) == 4) {
+    switch (op.k) {
+      case 1: dense_op_f2<1, 4>(v, m, op, U); return;
+      case 2: dense_op_f2<2, 2>(v, m, op, U); return;
+      case 3: dense_op_f2<3, 2>(v, m, op, U); return;
+      default: break;
+    }
   }
   switch (op.k) {
     // groups per trip: as many as the registers allow next to a thread's
