@@ -13,6 +13,7 @@
 // The ops themselves and the tile's shared-memory layout are in
 // tile_ops.cuh; tile passes with tensor-core blocks are in k_tile_tc.cu.
 #include <algorithm>
+#include <cstring>
 
 #include "tile_ops.cuh"
 
@@ -34,8 +35,9 @@ __device__ __forceinline__ void cp_async16(uint32_t smem, const void *gmem) {
 // The work of one CTA on one tile.  COH selects L2-coherent loads and stores
 // (bypassing L1), needed when other CTAs of the same launch wrote the tile
 // earlier (the persistent batch kernel); otherwise streaming hints are used.
-template <typename R, bool COH>
-__device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int b, unsigned char *smem_raw) {
+template <typename R, bool COH, bool INL = false>
+__device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int b, unsigned char *smem_raw,
+                                          const TileInline *I = nullptr) {
   using C = typename Cx<R>::T;
   const uint32_t TS = 1u << P.m;
   C *v0 = reinterpret_cast<C *>(smem_raw);
@@ -111,12 +113,20 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
 
   for (int oi = 0; oi < P.nops; oi++) {
     __syncthreads();
-    const TileOp op = P.ops[oi];
+    TileOp op;
+    if constexpr (INL) op = I->ops[oi];
+    else op = P.ops[oi];
     const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);
     switch (op.kind) {
       case TOP_DENSE:
       case TOP_DIAG: {
         if ((base & gcm) != gcm) break;
+        if constexpr (INL && sizeof(R) == 4) {
+          if (op.gen & kGenInline) {   // single vector: vmask is 1
+            apply_op_inl(reinterpret_cast<float2 *>(v0), P.m, op, *I);
+            break;
+          }
+        }
         const C *U = ((op.gen & kGenBatchMat) ? pmats : mats) + op.mat;
         if (op.vmask & 1) apply_op<R>(v0, P.m, op, P.ops + oi, U);
         if (op.vmask & 2) apply_op<R>(v1, P.m, op, P.ops + oi, U);
@@ -184,6 +194,39 @@ template <typename R>
 __global__ void __launch_bounds__(kTilePassThreads, kTilePassMinBlocks) k_tile(const __grid_constant__ TilePass P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   tile_body<R, false>(P, blockIdx.x, blockIdx.y, smem_raw);
+}
+
+// The same pass with its op list and small dense matrices in the parameter
+// block (complex64, one vector, one state).
+__global__ void __launch_bounds__(kTilePassThreads, kTilePassMinBlocks)
+    k_tile_inl(const __grid_constant__ TilePass P, const __grid_constant__ TileInline I) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tile_body<float, false, true>(P, blockIdx.x, 0, smem_raw, &I);
+}
+static_assert(sizeof(TilePass) + sizeof(TileInline) <= 32000, "kernel parameters exceed 32 KB");
+
+// Fill a parameter block from the host copy of a pass: all ops, and the
+// matrices of its single-vector 1-3 qubit dense blocks while they fit (the
+// rest keep their global matrices).  False when the op list does not fit.
+static bool build_inline(const TilePass &p, const HostPass &h, TileInline &I) {
+  if (p.nops > kInlOps) return false;
+  I.nops = (uint32_t)p.nops;
+  I.nmat = 0;
+  for (int i = 0; i < p.nops; i++) {
+    TileOp op = h.ops[i];
+    if (op.kind == TOP_DENSE && op.k <= 3 && op.gen == 0 && op.vmask == 1) {
+      const uint32_t cnt = 1u << (2 * op.k);
+      const uint32_t at = (I.nmat + 1u) & ~1u;    // rows are read in pairs
+      if (at + cnt <= (uint32_t)kInlMat) {
+        std::memcpy(&I.mats[at], h.mats + (size_t)op.mat * sizeof(float2), cnt * sizeof(float2));
+        op.mat = at;
+        op.gen = kGenInline;
+        I.nmat = at + cnt;
+      }
+    }
+    I.ops[i] = op;
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -284,7 +327,8 @@ sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
   return launch_tile_pass_on(s, p, batch, s->stream);
 }
 
-sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream) {
+sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream,
+                              const HostPass *host) {
   static bool attr_set[2][64] = {};
   if (p.flags & kPassHasTC) {
     if (s->dt != SV_C64 || p.m != kTcTileM || batch != 1 || p.nvec != 1)
@@ -295,16 +339,20 @@ sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStr
   const int dev = s->device & 63;
   const int di = s->dt == SV_C64 ? 0 : 1;
   if (!attr_set[di][dev]) {
-    if (s->dt == SV_C64)
+    if (s->dt == SV_C64) {
       SV_CUDA(cudaFuncSetAttribute(k_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
-    else
+      SV_CUDA(cudaFuncSetAttribute(k_tile_inl, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+    } else
       SV_CUDA(cudaFuncSetAttribute(k_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
     attr_set[di][dev] = true;
   }
   if (smem > (200u << 10)) return set_error(SV_EINVAL, "tile too large for shared memory");
   dim3 grid((unsigned)(1ull << (p.n - p.m)), (unsigned)batch);
   const int threads = tile_threads(p.m, s->dt);
-  if (s->dt == SV_C64)
+  TileInline inl;   // copied into the launch
+  if (host && s->dt == SV_C64 && batch == 1 && p.nvec == 1 && build_inline(p, *host, inl))
+    k_tile_inl<<<grid, threads, smem, stream>>>(p, inl);
+  else if (s->dt == SV_C64)
     k_tile<float><<<grid, threads, smem, stream>>>(p);
   else
     k_tile<double><<<grid, threads, smem, stream>>>(p);

@@ -279,8 +279,8 @@ sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, si
   return SV_OK;
 }
 
-sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream_t st) {
-  if (!(tp.flags & kPassTC)) return launch_tile_pass_on(s, tp, batch, st);
+sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream_t st, const HostPass *host) {
+  if (!(tp.flags & kPassTC)) return launch_tile_pass_on(s, tp, batch, st, host);
   int t[5];
   for (int j = 0; j < 5; j++) t[j] = tp.hi_pos[j];
   const uint32_t *b = reinterpret_cast<const uint32_t *>(static_cast<const char *>(tp.mats) + 16 * (size_t)tp.mat0);
@@ -305,7 +305,8 @@ sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &
     tp.v0 = E.v0;
     tp.v1 = E.v1;
     tp.err = reinterpret_cast<uint32_t *>(s->ws + kWsCtrl + kWsErrFlag);
-    SV_TRY(launch_any_pass(s, tp, E.batch, s->stream));
+    const HostPass hp{p.ops.data() + op0s[i], p.mats.data()};
+    SV_TRY(launch_any_pass(s, tp, E.batch, s->stream, &hp));
   }
   return SV_OK;
 }

@@ -161,7 +161,8 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
         tp.v0 = states[b]->amps;
         tp.nvec = 1;
         tp.err = reinterpret_cast<uint32_t *>(states[b]->ws + kWsCtrl + kWsErrFlag);
-        SV_TRY(launch_any_pass(states[b], tp, 1, st));
+        const HostPass hp{cp.prog.ops.data() + cp.op0s[p], cp.prog.mats.data()};
+        SV_TRY(launch_any_pass(states[b], tp, 1, st, &hp));
       }
       hkey = (hkey ^ keys[b] ^ (uint64_t)(uintptr_t)states[b]->amps) * 1099511628211ull;
     }

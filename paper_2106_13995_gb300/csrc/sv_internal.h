@@ -69,6 +69,18 @@ static_assert(sizeof(TileOp) == 32, "TileOp must stay 32 bytes");
 // Per-pass launch description (passed by value as a kernel parameter).
 constexpr int kMaxQ = 34;
 constexpr uint8_t kGenBatchMat = 0x80;   // TileOp.gen flag: matrix from the per-batch pool
+constexpr uint8_t kGenInline = 0x40;     // TileOp.gen flag: matrix in the launch's parameter block
+
+// Parameter block of a complex64 single-vector tile pass: its op list and
+// the matrices of its 1-3 qubit dense blocks, read by every CTA with
+// warp-uniform loads.  Passes that do not fit keep the global copies.
+constexpr int kInlOps = 48;
+constexpr int kInlMat = 3200;    // complex64 entries
+struct TileInline {
+  uint32_t nops, nmat;
+  TileOp ops[kInlOps];
+  float2 mats[kInlMat];
+};
 // TilePass.flags: this entry is not a tile pass but one 5-qubit dense block on
 // the tensor cores; hi_pos[0..4] hold its targets, mat0 the 16-byte index of
 // its packed operand in the matrix pool, bits 9..10 the sv_prec mode.
@@ -292,7 +304,13 @@ sv_status launch_sample_shots(sv_state *s, int64_t shot0, int64_t count, uint64_
 size_t sample_shot_offset(int n);
 int64_t sample_shot_capacity();
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch);
-sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream);
+// host copy of a pass's ops (the pass's first op) and of the program's matrix pool
+struct HostPass {
+  const TileOp *ops;
+  const uint8_t *mats;
+};
+sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream,
+                              const HostPass *host = nullptr);
 sv_status launch_tile_tc(sv_state *s, const TilePass &p, cudaStream_t stream);   // k_tile_tc.cu
 // tensor-core 5-qubit block (k_tc.cu)
 size_t tc_matrix_words(sv_prec mode);
@@ -300,7 +318,8 @@ void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t
 sv_status launch_dense_tc(sv_state *s, void *amps, const int *targets, const uint32_t *bmat_dev, sv_prec mode,
                           uint64_t spin_limit, cudaStream_t stream);
 // one pass of a program (tile pass or tensor-core block) on stream st
-sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream_t st);
+sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream_t st,
+                          const HostPass *host = nullptr);
 sv_status launch_tile_persist(sv_state *s, const PersistArgs &A, int m_max, int *grid_out, cudaStream_t st);
 sv_status launch_wait_selftest(cudaStream_t st, const uint32_t *never, uint32_t *err, uint64_t limit);
 int tile_threads(int m, sv_dtype dt);

@@ -223,9 +223,25 @@ __device__ __forceinline__ uint64_t lds_b64(uint32_t a) {
 // complex64 dense block with packed FP32 arithmetic: for output row r the
 // pair (re, im) accumulates Re(u) (x re, x im) and, separately,
 // Im(u) (x re, x im); the two combine into u x once per row.
-template <int K, int G>
+// Matrix rows of a dense block: from global memory through L1 (each 16-byte
+// load lands in all 32 lanes' registers), or from the launch's parameter
+// block, whose warp-uniform reads take the uniform datapath instead of the
+// L1 data pipe.
+struct GlobalRows {
+  const float2 *U;
+  __device__ __forceinline__ void operator()(int i, float2 &a, float2 &b) const { ld_pair(U + i, a, b); }
+};
+struct ParamRows {
+  const TileInline &I;
+  uint32_t base;
+  __device__ __forceinline__ void operator()(int i, float2 &a, float2 &b) const {
+    a = I.mats[base + i];
+    b = I.mats[base + i + 1];
+  }
+};
+template <int K, int G, class Rows>
 __device__ __forceinline__ void dense_op_f2(float2 *__restrict__ v, int m, const TileOp &op,
-                                            const float2 *__restrict__ U) {
+                                            const Rows &rows) {
   constexpr int D = 1 << K;
   constexpr bool kRegU = K <= 2;
   const uint32_t vs = smem_u32(v);
@@ -242,7 +258,7 @@ __device__ __forceinline__ void dense_op_f2(float2 *__restrict__ v, int m, const
   float2 ur[kRegU ? D * D : 1];
   if constexpr (kRegU) {
 #pragma unroll
-    for (int q = 0; q < D * D; q += 2) ld_pair(U + q, ur[q], ur[q + 1]);
+    for (int q = 0; q < D * D; q += 2) rows(q, ur[q], ur[q + 1]);
   }
   const uint32_t fixed = tmask | op.lcmask;
   const uint32_t ngroups = 1u << (m - __popc(fixed));
@@ -278,7 +294,7 @@ __device__ __forceinline__ void dense_op_f2(float2 *__restrict__ v, int m, const
           u0 = ur[(r * D + y) % (kRegU ? D * D : 1)];
           u1 = ur[(r * D + y + 1) % (kRegU ? D * D : 1)];
         } else {
-          ld_pair(U + r * D + y, u0, u1);
+          rows(r * D + y, u0, u1);
         }
         const uint64_t r0 = pk2(u0.x, u0.x), i0 = pk2(u0.y, u0.y);
         const uint64_t r1 = pk2(u1.x, u1.x), i1 = pk2(u1.y, u1.y);
@@ -297,6 +313,16 @@ __device__ __forceinline__ void dense_op_f2(float2 *__restrict__ v, int m, const
           sts_c(vs + (s[h] ^ soff[r]), make_float2(p.x - q.y, p.y + q.x));
         }
     }
+  }
+}
+
+// Dense complex64 block of 1-3 qubits whose matrix is in the launch's
+// parameter block (op.mat indexes TileInline::mats).
+__device__ __forceinline__ void apply_op_inl(float2 *v, int m, const TileOp &op, const TileInline &I) {
+  switch (op.k) {
+    case 1: dense_op_f2<1, 4>(v, m, op, ParamRows{I, op.mat}); break;
+    case 2: dense_op_f2<2, 2>(v, m, op, ParamRows{I, op.mat}); break;
+    default: dense_op_f2<3, 2>(v, m, op, ParamRows{I, op.mat}); break;
   }
 }
 
@@ -352,9 +378,9 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
   }
   if constexpr (sizeof(R) == 4) {
     switch (op.k) {
-      case 1: dense_op_f2<1, 4>(v, m, op, U); return;
-      case 2: dense_op_f2<2, 2>(v, m, op, U); return;
-      case 3: dense_op_f2<3, 2>(v, m, op, U); return;
+      case 1: dense_op_f2<1, 4>(v, m, op, GlobalRows{U}); return;
+      case 2: dense_op_f2<2, 2>(v, m, op, GlobalRows{U}); return;
+      case 3: dense_op_f2<3, 2>(v, m, op, GlobalRows{U}); return;
       default: break;
     }
   }

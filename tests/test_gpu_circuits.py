@@ -51,6 +51,26 @@ def test_mixed_random_all_fusions_and_tiles(svlib, oracle, dt, fk, m):
     assert inf <= tol, (inf, amp)
 
 
+@pytest.mark.parametrize("nops", [47, 48, 49, 200])
+def test_pass_op_list_around_parameter_block_size(svlib, oracle, nops):
+    """A complex64 pass keeps its op list and small dense matrices in the
+    launch's parameter block when the list fits (48 ops), and its global
+    copies otherwise: one 13-qubit pass of nops unfused blocks on each side
+    of that size agrees with the oracle."""
+    n = 13
+    rng = np.random.default_rng(nops)
+    c = W.Circuit(n)
+    for i in range(nops):
+        k = 1 + i % 3
+        t = tuple(int(x) for x in rng.choice(n, size=k, replace=False))
+        c.ops.append(W.Op("MATRIX", t, matrix=W.random_unitary(k, rng)))
+    opts = svlib.options(fusion_k=1, tile_m=n)
+    s = run_gpu(svlib, c, "c64", opts=opts)
+    assert s.plan_info(c, opts=opts) == (nops, 1)
+    inf, amp = fidelity_metrics(oracle.run(c), s.numpy())
+    assert inf <= 1e-5, (nops, inf, amp)
+
+
 @pytest.mark.parametrize("n", [3, 5, 9])
 def test_small_states_single_tile(svlib, oracle, n):
     c = W.random_gate_circuit(n, 40, seed=n, kmax=min(3, n))
