@@ -362,9 +362,9 @@ def main():
                 traffic = tr["dram_bytes_per_launch"]
         except Exception:
             traffic = None
-        kernel = {"plain": "k_tile<float> (tile pass)",
+        kernel = {"plain": "k_tile_inl (tile pass; op list and 1-3 qubit matrices in the parameter block)",
                   "bf16x3": "k_tile_tc (tile pass with tensor-core 5-qubit blocks)",
-                  "tf32x3": "k_tile<float> and k_dense_tc (tile passes and tensor-core passes)"}[args.prec]
+                  "tf32x3": "k_tile_inl and k_dense_tc (tile passes and tensor-core passes)"}[args.prec]
         if args.prec != "plain":
             traffic = None    # the stored capture is of the plain tile pass
         out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
