@@ -154,9 +154,19 @@ def pin_to_gpu_numa_node():
     allocates and touches next are local to the GPU.  Returns the node, or
     None when the topology is not available."""
     try:
-        bus = subprocess.run(["nvidia-smi", "--query-gpu=pci.bus_id", "--format=csv,noheader", "-i",
-                              os.environ.get("LOCAL_RANK", "0")], capture_output=True, text=True,
-                             timeout=20).stdout.strip().splitlines()[0].strip()
+        import torch
+        # nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES:
+        # find this process's GPU by its UUID
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid).lower()
+        rows = subprocess.run(["nvidia-smi", "--query-gpu=uuid,pci.bus_id", "--format=csv,noheader"],
+                              capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+        bus = None
+        for r in rows:
+            u, b = (x.strip() for x in r.split(",", 1))
+            if u.lower().removeprefix("gpu-") == uuid.removeprefix("gpu-"):
+                bus = b
+        if bus is None:
+            return None
         dom, rest = bus.split(":", 1)
         dev = f"{int(dom, 16):04x}:{rest.lower()}"
         node = int(open(f"/sys/bus/pci/devices/{dev}/numa_node").read().strip())
