@@ -148,39 +148,59 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle on host cores (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def pin_to_gpu_numa_node():
-    """Restrict this process to the CPUs of the GPU's NUMA node (read from
-    sysfs through the PCI bus id nvidia-smi reports), so host buffers it
-    allocates and touches next are local to the GPU.  Returns the node, or
-    None when the topology is not available."""
+def numa_nodes_with_cpus():
+    """{node: set of CPUs} for the host's NUMA nodes that have CPUs."""
+    out = {}
+    base = "/sys/devices/system/node"
     try:
-        import torch
-        # nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES:
-        # find this process's GPU by its UUID
-        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid).lower()
-        rows = subprocess.run(["nvidia-smi", "--query-gpu=uuid,pci.bus_id", "--format=csv,noheader"],
-                              capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
-        bus = None
-        for r in rows:
-            u, b = (x.strip() for x in r.split(",", 1))
-            if u.lower().removeprefix("gpu-") == uuid.removeprefix("gpu-"):
-                bus = b
-        if bus is None:
-            return None
-        dom, rest = bus.split(":", 1)
-        dev = f"{int(dom, 16):04x}:{rest.lower()}"
-        node = int(open(f"/sys/bus/pci/devices/{dev}/numa_node").read().strip())
-        if node < 0:
-            return None
+        names = sorted(x for x in os.listdir(base) if x.startswith("node") and x[4:].isdigit())
+    except OSError:
+        return out
+    for name in names:
+        try:
+            txt = open(f"{base}/{name}/cpulist").read().strip()
+        except OSError:
+            continue
         cpus = set()
-        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+        for part in filter(None, txt.split(",")):
             a, _, b = part.partition("-")
             cpus.update(range(int(a), int(b or a) + 1))
         if cpus:
+            out[int(name[4:])] = cpus
+    return out
+
+
+def pin_to_fastest_host_node(torch, dev):
+    """Restrict this process to the CPUs of the NUMA node whose pinned memory
+    copies to the GPU fastest (a 256 MiB probe per node: sysfs does not
+    always name the node a GPU is attached to), so host buffers allocated
+    next land there.  Returns (node, {node: probe GB/s}); the caller restores
+    the affinity after allocating."""
+    nodes = numa_nodes_with_cpus()
+    if not nodes:
+        return None, {}
+    rates = {}
+    dst = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    for node, cpus in nodes.items():
+        try:
             os.sched_setaffinity(0, cpus)
-        return node
-    except Exception:
-        return None
+            buf = torch.ones(64 << 20, dtype=torch.float32, pin_memory=True)
+            dst.copy_(buf, non_blocking=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(3):
+                dst.copy_(buf, non_blocking=True)
+            torch.cuda.synchronize()
+            rates[node] = 3 * buf.numel() * 4 / (time.perf_counter() - t0) / 1e9
+            del buf
+        except Exception:
+            continue
+    del dst
+    if not rates:
+        return None, {}
+    best = max(rates, key=rates.get)
+    os.sched_setaffinity(0, nodes[best])
+    return best, {str(k): round(v, 1) for k, v in rates.items()}
 
 
 def oracle_sample(circ, budget_s: float, max_gates=None):
@@ -324,7 +344,7 @@ def main():
     # ---- end to end through the C ABI from host buffers -----------------------
     if "e2e" in sections:
         aff = os.sched_getaffinity(0)
-        numa = pin_to_gpu_numa_node()   # pinned pages land on the GPU's NUMA node
+        numa, probe = pin_to_fastest_host_node(torch, dev)   # pinned pages land on that node
         host = torch.zeros(2 << n, dtype=torch.float32, pin_memory=True)
         os.sched_setaffinity(0, aff)
         host[0] = 1.0
@@ -352,7 +372,7 @@ def main():
         out["e2e"] = {"value": len(circ.ops) * ke * world / te, "unit": UNIT,
                       "h2d_bytes_per_step": state.nbytes, "d2h_bytes_per_step": 8 * n + 8 + 8 * 1000,
                       "ms_per_step": 1e3 * te / ke, "h2d_gbs": state.nbytes / tu / 1e9,
-                      "host_numa_node": numa}
+                      "host_numa_node": numa, "h2d_probe_gbs_by_node": probe}
         del host
 
     # ---- roofline of the dominant kernel (the tile pass) -----------------------

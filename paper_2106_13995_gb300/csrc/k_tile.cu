@@ -126,10 +126,17 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
             apply_op_inl(reinterpret_cast<float2 *>(v0), P.m, op, *I);
             break;
           }
+          if (op.kind == TOP_DENSE && op.k <= 3) {
+            // the host launches this kernel only when every such block is in
+            // the parameter block; report a broken invariant instead of
+            // computing without the block
+            if (threadIdx.x == 0) atomicOr(P.err, kErrNoInlineBlock);
+            break;
+          }
         }
         const C *U = ((op.gen & kGenBatchMat) ? pmats : mats) + op.mat;
-        if (op.vmask & 1) apply_op<R>(v0, P.m, op, P.ops + oi, U);
-        if (op.vmask & 2) apply_op<R>(v1, P.m, op, P.ops + oi, U);
+        if (op.vmask & 1) apply_op<R, INL>(v0, P.m, op, P.ops + oi, U);
+        if (op.vmask & 2) apply_op<R, INL>(v1, P.m, op, P.ops + oi, U);
         break;
       }
       case TOP_GRAD:
@@ -206,23 +213,23 @@ __global__ void __launch_bounds__(kTilePassThreads, kTilePassMinBlocks)
 static_assert(sizeof(TilePass) + sizeof(TileInline) <= 32000, "kernel parameters exceed 32 KB");
 
 // Fill a parameter block from the host copy of a pass: all ops, and the
-// matrices of its single-vector 1-3 qubit dense blocks while they fit (the
-// rest keep their global matrices).  False when the op list does not fit.
+// matrices of its 1-3 qubit dense blocks (already in the row-pair layout).
+// False unless every such block fits (the kernel has no other path for
+// them).
 static bool build_inline(const TilePass &p, const HostPass &h, TileInline &I) {
   if (p.nops > kInlOps) return false;
   I.nops = (uint32_t)p.nops;
   I.nmat = 0;
   for (int i = 0; i < p.nops; i++) {
     TileOp op = h.ops[i];
-    if (op.kind == TOP_DENSE && op.k <= 3 && op.gen == 0 && op.vmask == 1) {
+    if (op.kind == TOP_DENSE && op.k <= 3) {
       const uint32_t cnt = 1u << (2 * op.k);
-      const uint32_t at = (I.nmat + 1u) & ~1u;    // rows are read in pairs
-      if (at + cnt <= (uint32_t)kInlMat) {
-        std::memcpy(&I.mats[at], h.mats + (size_t)op.mat * sizeof(float2), cnt * sizeof(float2));
-        op.mat = at;
-        op.gen = kGenInline;
-        I.nmat = at + cnt;
-      }
+      const uint32_t at = I.nmat;
+      if (op.gen != 0 || op.vmask != 1 || at + cnt > (uint32_t)kInlMat) return false;
+      std::memcpy(&I.mats[at], h.mats + (size_t)op.mat * sizeof(float2), cnt * sizeof(float2));
+      op.mat = at;
+      op.gen = kGenInline;
+      I.nmat = at + cnt;
     }
     I.ops[i] = op;
   }

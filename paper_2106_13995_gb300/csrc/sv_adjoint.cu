@@ -148,10 +148,14 @@ static void put_mats(std::vector<uint8_t> &pool, const AdjointProgram &A, const 
       const double ang[3] = {theta[A.inst_param[i]], 0, 0};
       gate_matrix(A.inst_gate[i], ang, U);
       if (pass == 1) U = adjoint_of(U, 1);
-      for (int e = 0; e < 4; e++) {
-        R v[2] = {(R)U[e].real(), (R)U[e].imag()};
-        const uint8_t *p = (const uint8_t *)v;
-        pool.insert(pool.end(), p, p + sizeof(v));
+      if constexpr (sizeof(R) == 4) {
+        put_pairs_c64(pool, U.data(), 1);   // the layout complex64 tile ops read
+      } else {
+        for (int e = 0; e < 4; e++) {
+          R v[2] = {(R)U[e].real(), (R)U[e].imag()};
+          const uint8_t *p = (const uint8_t *)v;
+          pool.insert(pool.end(), p, p + sizeof(v));
+        }
       }
     }
 }

@@ -146,6 +146,17 @@ static void set_thread_positions(TileOp &op, uint32_t fixed, int m, sv_dtype dt)
   for (int i = 0; i < nf; i++) op.tbpos[i >> 1] |= (uint8_t)(P[i] << (4 * (i & 1)));
 }
 
+void put_pairs_c64(std::vector<uint8_t> &pool, const cd *U, int k) {
+  const int d = 1 << k;
+  for (int p = 0; p < d / 2; p++)
+    for (int y = 0; y < d; y++) {
+      const cd a = U[(size_t)(2 * p) * d + y], b = U[(size_t)(2 * p + 1) * d + y];
+      const float v[4] = {(float)a.real(), (float)b.real(), (float)a.imag(), (float)b.imag()};
+      const uint8_t *q = reinterpret_cast<const uint8_t *>(v);
+      pool.insert(pool.end(), q, q + sizeof(v));
+    }
+}
+
 // Convert one planned pass into TilePass + TileOps (+ matrices).
 sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
                            std::vector<uint32_t> &op0s, const std::vector<int> &batch_mat_off) {
@@ -197,6 +208,8 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
           for (int r = 0; r < d; r++)
             b.dt == SV_C64 ? put_c<float>(prog.mats, blk.U[(size_t)r * d + r])
                            : put_c<double>(prog.mats, blk.U[(size_t)r * d + r]);
+        } else if (b.dt == SV_C64 && op.k <= 3) {
+          put_pairs_c64(prog.mats, blk.U.data(), op.k);
         } else {
           for (int e = 0; e < d * d; e++)
             b.dt == SV_C64 ? put_c<float>(prog.mats, blk.U[e]) : put_c<double>(prog.mats, blk.U[e]);
@@ -568,8 +581,11 @@ sv_status sv_synchronize(sv_state *s) {
   SV_CUDA(cudaMemcpyAsync(host, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
   SV_CUDA(cudaStreamSynchronize(s->stream));
   if (*host) {
+    const uint32_t bits = *host;
     SV_CUDA(cudaMemsetAsync(flag, 0, sizeof(uint32_t), s->stream));
     SV_CUDA(cudaStreamSynchronize(s->stream));
+    if (bits & kErrNoInlineBlock)
+      return set_error(SV_EUNSUPPORTED, "internal: a tile pass met a block missing from its parameter block");
     return set_error(SV_ETIMEOUT, "a bounded device wait ran out; the last batch is incomplete");
   }
   return SV_OK;

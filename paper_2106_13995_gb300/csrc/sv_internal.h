@@ -73,7 +73,8 @@ constexpr uint8_t kGenInline = 0x40;     // TileOp.gen flag: matrix in the launc
 
 // Parameter block of a complex64 single-vector tile pass: its op list and
 // the matrices of its 1-3 qubit dense blocks, read by every CTA with
-// warp-uniform loads.  Passes that do not fit keep the global copies.
+// warp-uniform loads (matrices as row pairs, see dense_pairs).  Passes that
+// do not fit keep the global copies.
 constexpr int kInlOps = 48;
 constexpr int kInlMat = 3200;    // complex64 entries
 struct TileInline {
@@ -233,7 +234,9 @@ size_t amp_bytes(sv_dtype dt);
 int lmin(sv_dtype dt);            // low qubits a tile must keep contiguous (16-byte copies)
 int mmax(sv_dtype dt, int nvec);  // largest tile that fits shared memory
 constexpr size_t kWsScalars = 0;            // FP64 result slots (4 KB)
-constexpr size_t kWsErrFlag = 3072;         // uint32 set by a bounded device wait that ran out
+constexpr size_t kWsErrFlag = 3072;         // uint32 device error bits (below)
+constexpr uint32_t kErrWaitTimeout = 1u;     // a bounded device wait ran out
+constexpr uint32_t kErrNoInlineBlock = 2u;   // a parameter-block tile pass met a block outside it
 constexpr size_t kWsGateMat = 64 << 10;     // single-gate matrix scratch (k >= 4)
 
 // program building / upload / launch (sv_api.cu)
@@ -304,6 +307,10 @@ sv_status launch_sample_shots(sv_state *s, int64_t shot0, int64_t count, uint64_
 size_t sample_shot_offset(int n);
 int64_t sample_shot_capacity();
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch);
+// Append a complex64 dense matrix of k <= 3 qubits (row-major U) to a pool
+// in the row-pair layout the packed tile ops read: for p < 2^k / 2 and
+// column y, (Re U[2p][y], Re U[2p+1][y]) then (Im U[2p][y], Im U[2p+1][y]).
+void put_pairs_c64(std::vector<uint8_t> &pool, const cd *U, int k);
 // host copy of a pass's ops (the pass's first op) and of the program's matrix pool
 struct HostPass {
   const TileOp *ops;

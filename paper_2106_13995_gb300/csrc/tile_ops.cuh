@@ -220,30 +220,41 @@ __device__ __forceinline__ uint64_t lds_b64(uint32_t a) {
   return r;
 }
 
-// complex64 dense block with packed FP32 arithmetic: for output row r the
-// pair (re, im) accumulates Re(u) (x re, x im) and, separately,
-// Im(u) (x re, x im); the two combine into u x once per row.
-// Matrix rows of a dense block: from global memory through L1 (each 16-byte
-// load lands in all 32 lanes' registers), or from the launch's parameter
-// block, whose warp-uniform reads take the uniform datapath instead of the
-// L1 data pipe.
-struct GlobalRows {
-  const float2 *U;
-  __device__ __forceinline__ void operator()(int i, float2 &a, float2 &b) const { ld_pair(U + i, a, b); }
-};
-struct ParamRows {
+// complex64 dense blocks of 1-3 qubits in packed FP32 arithmetic, columns
+// outermost.  For output rows (2p, 2p+1) the packed accumulators hold
+//   re = sum_y (Re U[2p][y], Re U[2p+1][y]) * (Re x_y, Re x_y)
+//   tt = sum_y (Im U[2p][y], Im U[2p+1][y]) * (Im x_y, Im x_y)
+//   im = sum_y (Re U .. ) * (Im x_y, Im x_y) + (Im U .. ) * (Re x_y, Re x_y)
+// and the outputs are (re - tt, im) per row.  Each input amplitude is read
+// once and broadcast into two pairs that feed every row pair; a group's
+// outputs are written after its last column.  The matrix arrives as the
+// row pairs (Re U[2p][y], Re U[2p+1][y]), (Im U[2p][y], Im U[2p+1][y]),
+// the layout the host stores complex64 blocks of 1-3 qubits in: read from
+// the launch's parameter block (warp-uniform reads take the uniform
+// datapath) or from global memory through L1, with the same arithmetic, so
+// every kernel that applies these blocks produces the same bits.
+struct ParamPairs {
   const TileInline &I;
   uint32_t base;
-  __device__ __forceinline__ void operator()(int i, float2 &a, float2 &b) const {
-    a = I.mats[base + i];
-    b = I.mats[base + i + 1];
+  template <int D>
+  __device__ __forceinline__ void pair(int p, int y, uint64_t &ur, uint64_t &ui) const {
+    const uint64_t *M = reinterpret_cast<const uint64_t *>(&I.mats[base]);
+    ur = M[(p * D + y) * 2];
+    ui = M[(p * D + y) * 2 + 1];
   }
 };
-template <int K, int G, class Rows>
-__device__ __forceinline__ void dense_op_f2(float2 *__restrict__ v, int m, const TileOp &op,
-                                            const Rows &rows) {
-  constexpr int D = 1 << K;
-  constexpr bool kRegU = K <= 2;
+struct GlobalPairs {
+  const float2 *U;   // row pairs, 16-byte aligned
+  template <int D>
+  __device__ __forceinline__ void pair(int p, int y, uint64_t &ur, uint64_t &ui) const {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(U + (p * D + y) * 2));
+    ur = pk2(q.x, q.y);
+    ui = pk2(q.z, q.w);
+  }
+};
+template <int K, int G, class Src>
+__device__ __forceinline__ void dense_pairs(float2 *__restrict__ v, int m, const TileOp &op, const Src &src) {
+  constexpr int D = 1 << K, NP = D / 2;
   const uint32_t vs = smem_u32(v);
   uint32_t soff[D], tmask = 0;
   soff[0] = 0;
@@ -255,15 +266,12 @@ __device__ __forceinline__ void dense_op_f2(float2 *__restrict__ v, int m, const
 #pragma unroll
     for (int y = 0; y < (1 << j); y++) soff[y + (1 << j)] = soff[y] ^ e;
   }
-  float2 ur[kRegU ? D * D : 1];
-  if constexpr (kRegU) {
-#pragma unroll
-    for (int q = 0; q < D * D; q += 2) rows(q, ur[q], ur[q + 1]);
-  }
   const uint32_t fixed = tmask | op.lcmask;
   const uint32_t ngroups = 1u << (m - __popc(fixed));
   const uint32_t T = blockDim.x;
   if (threadIdx.x >= ngroups) return;
+  // thread t's groups are t + c T, c < ntrips; slot(t + c T) = slot(t) ^
+  // slot(c T), and a trip's G groups c0 + h share slot(c0 T)
   const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
   const uint32_t sthr = swb<float>(thread_l(threadIdx.x, op) | op.lcmask);
   const TripMap tm = trip_map(T, fixed);
@@ -273,56 +281,78 @@ __device__ __forceinline__ void dense_op_f2(float2 *__restrict__ v, int m, const
   for (uint32_t c0 = 0; c0 < ntrips; c0 += G) {
     uint32_t s[G];
     bool ok[G];
-    uint64_t x[G][D];
     const uint32_t sc = sthr ^ swb<float>(trip_l(c0, tm));
 #pragma unroll
     for (int h = 0; h < G; h++) {
       ok[h] = c0 + h < ntrips;
       s[h] = ok[h] ? sc ^ dh[h] : sthr;
-#pragma unroll
-      for (int y = 0; y < D; y++) x[h][y] = lds_b64(vs + (s[h] ^ soff[y]));
     }
+    uint64_t re[NP][G], tt[NP][G], im[NP][G];
 #pragma unroll
-    for (int r = 0; r < D; r++) {
-      uint64_t a1[G], a2[G];
+    for (int p = 0; p < NP; p++)
 #pragma unroll
-      for (int h = 0; h < G; h++) a1[h] = a2[h] = 0ull;
+      for (int h = 0; h < G; h++) re[p][h] = tt[p][h] = im[p][h] = 0ull;
 #pragma unroll
-      for (int y = 0; y < D; y += 2) {
-        float2 u0, u1;
-        if constexpr (kRegU) {
-          u0 = ur[(r * D + y) % (kRegU ? D * D : 1)];
-          u1 = ur[(r * D + y + 1) % (kRegU ? D * D : 1)];
-        } else {
-          rows(r * D + y, u0, u1);
-        }
-        const uint64_t r0 = pk2(u0.x, u0.x), i0 = pk2(u0.y, u0.y);
-        const uint64_t r1 = pk2(u1.x, u1.x), i1 = pk2(u1.y, u1.y);
+    for (int y = 0; y < D; y++) {
+      uint64_t xr[G], xi[G];
+#pragma unroll
+      for (int h = 0; h < G; h++) {
+        const float2 x = upk2(lds_b64(vs + (s[h] ^ soff[y])));
+        xr[h] = pk2(x.x, x.x);
+        xi[h] = pk2(x.y, x.y);
+      }
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        uint64_t ur, ui;
+        src.template pair<D>(p, y, ur, ui);
 #pragma unroll
         for (int h = 0; h < G; h++) {
-          a1[h] = fma2(r0, x[h][y], a1[h]);
-          a2[h] = fma2(i0, x[h][y], a2[h]);
-          a1[h] = fma2(r1, x[h][y + 1], a1[h]);
-          a2[h] = fma2(i1, x[h][y + 1], a2[h]);
+          re[p][h] = fma2(ur, xr[h], re[p][h]);
+          tt[p][h] = fma2(ui, xi[h], tt[p][h]);
+          im[p][h] = fma2(ur, xi[h], im[p][h]);
+          im[p][h] = fma2(ui, xr[h], im[p][h]);
         }
       }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; p++)
 #pragma unroll
       for (int h = 0; h < G; h++)
         if (ok[h]) {
-          const float2 p = upk2(a1[h]), q = upk2(a2[h]);
-          sts_c(vs + (s[h] ^ soff[r]), make_float2(p.x - q.y, p.y + q.x));
+          const float2 a = upk2(re[p][h]), b = upk2(tt[p][h]), c = upk2(im[p][h]);
+          sts_c(vs + (s[h] ^ soff[2 * p]), make_float2(a.x - b.x, c.x));
+          sts_c(vs + (s[h] ^ soff[2 * p + 1]), make_float2(a.y - b.y, c.y));
         }
-    }
+  }
+}
+
+// groups per trip of the packed blocks (registers: three packed
+// accumulators per row pair and group); the grouping does not change the
+// arithmetic
+template <int K> constexpr int kPairsG = K <= 2 ? 4 : 2;
+
+// groups per trip with matrices in global memory (batched, two-vector and
+// tensor-core passes, ops beyond a parameter block): the loaded pairs take
+// ordinary registers, so 3-qubit blocks run one group per trip
+template <int K> constexpr int kPairsGlobalG = K == 1 ? 4 : (K == 2 ? 2 : 1);
+
+__device__ __forceinline__ void dense_pairs_global(float2 *v, int m, const TileOp &op, const float2 *U) {
+  const GlobalPairs src{U};
+  switch (op.k) {
+    case 1: dense_pairs<1, kPairsGlobalG<1>>(v, m, op, src); break;
+    case 2: dense_pairs<2, kPairsGlobalG<2>>(v, m, op, src); break;
+    default: dense_pairs<3, kPairsGlobalG<3>>(v, m, op, src); break;
   }
 }
 
 // Dense complex64 block of 1-3 qubits whose matrix is in the launch's
-// parameter block (op.mat indexes TileInline::mats).
+// parameter block (op.mat indexes TileInline::mats, stored as row pairs).
 __device__ __forceinline__ void apply_op_inl(float2 *v, int m, const TileOp &op, const TileInline &I) {
+  const ParamPairs src{I, op.mat};
   switch (op.k) {
-    case 1: dense_op_f2<1, 4>(v, m, op, ParamRows{I, op.mat}); break;
-    case 2: dense_op_f2<2, 2>(v, m, op, ParamRows{I, op.mat}); break;
-    default: dense_op_f2<3, 2>(v, m, op, ParamRows{I, op.mat}); break;
+    case 1: dense_pairs<1, kPairsG<1>>(v, m, op, src); break;
+    case 2: dense_pairs<2, kPairsG<2>>(v, m, op, src); break;
+    default: dense_pairs<3, kPairsG<3>>(v, m, op, src); break;
   }
 }
 
@@ -369,7 +399,10 @@ __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m
   }
 }
 
-template <typename R>
+// kSmallInParams: the kernel takes complex64 dense blocks of 1-3 qubits from
+// its parameter block and never here (leaving that code out keeps its
+// registers off the hot path)
+template <typename R, bool kSmallInParams = false>
 __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const TileOp &op, const TileOp *gop,
                                          const typename Cx<R>::T *U) {
   if (op.kind == TOP_DIAG) {
@@ -377,11 +410,11 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
     return;
   }
   if constexpr (sizeof(R) == 4) {
-    switch (op.k) {
-      case 1: dense_op_f2<1, 4>(v, m, op, GlobalRows{U}); return;
-      case 2: dense_op_f2<2, 2>(v, m, op, GlobalRows{U}); return;
-      case 3: dense_op_f2<3, 2>(v, m, op, GlobalRows{U}); return;
-      default: break;
+    if constexpr (!kSmallInParams) {
+      if (op.k <= 3) {
+        dense_pairs_global(v, m, op, U);
+        return;
+      }
     }
   }
   switch (op.k) {
