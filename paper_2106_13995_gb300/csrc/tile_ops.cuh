@@ -336,12 +336,15 @@ template <int K> constexpr int kPairsG = K <= 2 ? 4 : 2;
 // ordinary registers, so 3-qubit blocks run one group per trip
 template <int K> constexpr int kPairsGlobalG = K == 1 ? 4 : (K == 2 ? 2 : 1);
 
+// WIDE: the kernel has registers to spare (128 a thread): two groups per
+// trip for 3-qubit blocks
+template <bool WIDE = false>
 __device__ __forceinline__ void dense_pairs_global(float2 *v, int m, const TileOp &op, const float2 *U) {
   const GlobalPairs src{U};
   switch (op.k) {
     case 1: dense_pairs<1, kPairsGlobalG<1>>(v, m, op, src); break;
     case 2: dense_pairs<2, kPairsGlobalG<2>>(v, m, op, src); break;
-    default: dense_pairs<3, kPairsGlobalG<3>>(v, m, op, src); break;
+    default: dense_pairs<3, WIDE ? 2 : kPairsGlobalG<3>>(v, m, op, src); break;
   }
 }
 
@@ -402,7 +405,7 @@ __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m
 // kSmallInParams: the kernel takes complex64 dense blocks of 1-3 qubits from
 // its parameter block and never here (leaving that code out keeps its
 // registers off the hot path)
-template <typename R, bool kSmallInParams = false>
+template <typename R, bool kSmallInParams = false, bool kWideRegs = false>
 __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const TileOp &op, const TileOp *gop,
                                          const typename Cx<R>::T *U) {
   if (op.kind == TOP_DIAG) {
@@ -412,7 +415,7 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
   if constexpr (sizeof(R) == 4) {
     if constexpr (!kSmallInParams) {
       if (op.k <= 3) {
-        dense_pairs_global(v, m, op, U);
+        dense_pairs_global<kWideRegs>(v, m, op, U);
         return;
       }
     }
