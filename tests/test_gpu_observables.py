@@ -25,6 +25,33 @@ def test_expect_random_paulis(svlib, oracle, dt, tol):
         assert abs(s.norm2() - oracle.norm2(cast)) <= tol
 
 
+@pytest.mark.parametrize("dt,tol", [("c64", 2e-6), ("c128", 1e-12)])
+def test_expect_diagonal_groups(svlib, oracle, dt, tol):
+    """Groups of Z strings only (x mask 0): random strings of weight 0..4
+    over low and high bits, the same mask with several coefficients, and
+    nearest-neighbour ZZ terms, at widths around the reduction kernels'
+    run and chunk sizes."""
+    rng = np.random.default_rng(7)
+    for n in (7, 8, 9, 10, 14, 20):
+        psi = W.random_state(n, rng)
+        s = svlib.StateVector(n, dt).load(psi)
+        cast = s.numpy().astype(np.complex128)
+        terms = []
+        for _ in range(40):
+            w = int(rng.integers(0, 5))
+            z = 0
+            for q in rng.choice(n, size=min(w, n), replace=False):
+                z |= 1 << int(q)
+            terms.append((0, z, float(rng.normal())))
+        terms += [(0, terms[3][1], 0.5), (0, terms[3][1], -0.25)]
+        terms += [(0, (1 << q) | (1 << (q + 1)), 1.0) for q in range(n - 1)][:20]
+        want = oracle.expect(cast, terms)
+        got = s.expect(terms)
+        scale = sum(abs(t[2]) for t in terms)
+        assert abs(got - want) <= tol * scale, (n, got, want)
+        s.close()
+
+
 def test_z_all_large(svlib, oracle):
     n = 22
     c = W.random_u3_cz(n, 2, 11)
