@@ -401,6 +401,20 @@ def main():
                            "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                            "algorithmic_bytes_per_launch": gate_bytes, "launches_per_circuit": npasses,
                            "avg_launch_ms": per_launch * 1e3, "peak_source": peak_src}
+        # the same passes against the FP32 FMA rate: after fusion a pass does
+        # tens of multiply-adds per amplitude it moves, so instruction issue,
+        # not HBM, bounds it; flops = 2 x (planned multiply-adds per amplitude)
+        # x 2^n, peak = SMs x 128 FP32 lanes x 2 flops x the maximum SM clock
+        if args.prec == "plain":
+            fmas = state.plan_fmas(m, opts=step_opts)
+            flops = 2.0 * fmas * (1 << n)
+            mhz = out["clocks"].get("sm_max_mhz") or 2070.0
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            alu_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+            out["roofline_alu"] = {"bound": "alu", "achieved": flops / tc / 1e12, "peak": alu_peak,
+                                   "unit": "TFLOP/s", "frac": flops / tc / 1e12 / alu_peak,
+                                   "fma_per_amplitude": fmas, "flops_per_circuit": flops, "kernel": kernel,
+                                   "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz"}
 
     # ---- the same circuit with fused 5-qubit blocks on the tensor cores ----------
     if "tc" in sections:

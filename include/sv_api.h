@@ -189,6 +189,18 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *param
 sv_status sv_plan_info(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
                        int64_t *n_blocks, int64_t *n_passes);
 
+/* The arithmetic of that plan: real multiply-adds per state amplitude,
+ * summed over its fused blocks.  A dense k-qubit block with c controls
+ * costs 4 * 2^k / 2^c (each affected amplitude takes 2^k complex
+ * multiply-adds of 4 real ones), a diagonal block 4 / 2^c; blocks run on
+ * the tensor cores count as dense.  This is the work the tile passes'
+ * arithmetic roofline counts (times 2^n amplitudes, 2 flops each).
+ *   fma_per_amp: host pointer, receives the sum.
+ * Builds and caches the plan; launches nothing.  Same errors as
+ * sv_apply_circuit, and SV_EINVAL when fma_per_amp is NULL. */
+sv_status sv_plan_fmas(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
+                       double *fma_per_amp);
+
 /* Apply circs[b] (with parameters params[b], host FP64, either may repeat)
  * to states[b] for b < B, states of any widths, in ONE persistent launch:
  * every circuit is fused and planned into tile passes as by

@@ -82,6 +82,7 @@ def lib():
             "sv_apply_circuit": (st, [vp, C.POINTER(SvCircuit), dp, C.POINTER(SvOptions)]),
             "sv_plan_info": (st, [vp, C.POINTER(SvCircuit), dp, C.POINTER(SvOptions), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
+            "sv_plan_fmas": (st, [vp, C.POINTER(SvCircuit), dp, C.POINTER(SvOptions), dp]),
             "sv_apply_circuit_batch": (st, [C.POINTER(vp), C.c_int, C.POINTER(C.POINTER(SvCircuit)),
                                             C.POINTER(dp), C.POINTER(SvOptions)]),
             "sv_expect": (st, [vp, C.POINTER(SvPauliTerm), C.c_int, dp]),

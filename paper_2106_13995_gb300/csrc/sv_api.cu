@@ -652,4 +652,21 @@ sv_status sv_plan_info(sv_state *s, const sv_circuit *c, const double *params, c
   return SV_OK;
 }
 
+sv_status sv_plan_fmas(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
+                       double *fma_per_amp) {
+  if (!fma_per_amp) return set_error(SV_EINVAL, "null argument");
+  const CachedProgram *cp = nullptr;
+  uint64_t key = 0;
+  Opts o;
+  SV_TRY(get_program(s, c, params, opt, &cp, &key, &o));
+  double f = 0;
+  for (const Block &b : cp->blocks) {
+    if (b.kind != TOP_DENSE) continue;
+    const double share = std::ldexp(1.0, -(int)b.controls.size());
+    f += b.diag ? 4.0 * share : 4.0 * std::ldexp(1.0, (int)b.qubits.size()) * share;
+  }
+  *fma_per_amp = f;
+  return SV_OK;
+}
+
 }  // extern "C"

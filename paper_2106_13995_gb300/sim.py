@@ -161,6 +161,14 @@ class StateVector:
                                      C.byref(nb), C.byref(npass)))
         return nb.value, npass.value
 
+    def plan_fmas(self, circ, params: Optional[np.ndarray] = None, opts: Optional[N.SvOptions] = None) -> float:
+        """Real multiply-adds per amplitude of the planned blocks."""
+        m = marshal(circ)
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+        f = C.c_double()
+        N.check(N.lib().sv_plan_fmas(self.h, m.ref(), _dptr(p), C.byref(opts) if opts else None, C.byref(f)))
+        return f.value
+
     # -- observables ---------------------------------------------------------
     def expect(self, terms) -> float:
         arr, nt = pauli_terms(terms)

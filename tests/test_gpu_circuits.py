@@ -71,6 +71,34 @@ def test_pass_op_list_around_parameter_block_size(svlib, oracle, nops):
     assert inf <= 1e-5, (nops, inf, amp)
 
 
+def test_plan_fmas_counts_blocks(svlib):
+    """sv_plan_fmas: 4 * 2^k / 2^c real multiply-adds per amplitude for a
+    dense k-qubit block with c controls, 4 / 2^c for a diagonal one."""
+    n = 6
+    s = svlib.StateVector(n, "c64")
+    one = svlib.options(fusion_k=1)
+    c = W.Circuit(n)
+    c.ops += [W.Op("H", (q,)) for q in range(n)]
+    assert s.plan_fmas(c, opts=one) == 8.0 * n
+    c = W.Circuit(n)
+    c.ops += [W.Op("RZ", (q,), angles=(0.3,)) for q in range(n)]
+    assert s.plan_fmas(c, opts=one) == 4.0 * n
+    c = W.Circuit(n)
+    c.ops.append(W.Op("X", (0,), (1, 2)))                     # Toffoli: 8 / 4
+    assert s.plan_fmas(c, opts=one) == 2.0
+    rng = np.random.default_rng(3)
+    c = W.Circuit(n)
+    c.ops.append(W.Op("MATRIX", (0, 1, 2), matrix=W.random_unitary(3, rng)))
+    assert s.plan_fmas(c) == 32.0
+    g = W.grid_random(4, 4, 8, 1)
+    s16 = svlib.StateVector(16, "c64")
+    nb, _ = s16.plan_info(g)
+    f = s16.plan_fmas(g)
+    assert 8.0 * nb <= f <= 32.0 * nb
+    s.close()
+    s16.close()
+
+
 @pytest.mark.parametrize("n", [3, 5, 9])
 def test_small_states_single_tile(svlib, oracle, n):
     c = W.random_gate_circuit(n, 40, seed=n, kmax=min(3, n))
