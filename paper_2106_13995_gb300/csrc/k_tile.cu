@@ -123,7 +123,7 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
         if ((base & gcm) != gcm) break;
         if constexpr (INL && sizeof(R) == 4) {
           if (op.gen & kGenInline) {   // single vector: vmask is 1
-            apply_op_inl(reinterpret_cast<float2 *>(v0), P.m, op, *I);
+            apply_op_inl(reinterpret_cast<float2 *>(v0), P.m, op, *I, oi);
             break;
           }
           if (op.kind == TOP_DENSE && op.k <= 3) {
@@ -216,7 +216,43 @@ static_assert(sizeof(TilePass) + sizeof(TileInline) <= 32000, "kernel parameters
 // matrices of its 1-3 qubit dense blocks (already in the row-pair layout).
 // False unless every such block fits (the kernel has no other path for
 // them).
-static bool build_inline(const TilePass &p, const HostPass &h, TileInline &I) {
+// host copies of the device's index maps (tile_ops.cuh), for OpPre
+static uint32_t h_swb(uint32_t l) { return (l ^ ((l >> 4) & 15u)) * (uint32_t)sizeof(float2); }
+static uint32_t h_ins0_mask(uint32_t x, uint32_t fixed) {
+  for (; fixed; fixed &= fixed - 1) {
+    const int p = __builtin_ctz(fixed);
+    const uint32_t low = x & ((1u << p) - 1);
+    x = ((x ^ low) << 1) | low;
+  }
+  return x;
+}
+
+static void fill_pre(const TileOp &op, int threads, OpPre &pre) {
+  std::memset(&pre, 0, sizeof(pre));
+  uint32_t fixed = op.lcmask;
+  pre.soff[0] = 0;
+  for (int j = 0; j < op.k; j++) {
+    const uint32_t bit = 1u << op.t[j];
+    fixed |= bit;
+    for (int y = 0; y < (1 << j); y++) pre.soff[y + (1 << j)] = pre.soff[y] ^ h_swb(bit);
+  }
+  // trip map for T = threads (a power of two): fixed bits up to the trip
+  // region shift it, the ones above are inserted per trip
+  uint32_t low = (uint32_t)__builtin_ctz((uint32_t)threads), f = fixed;
+  while (f) {
+    const uint32_t q = (uint32_t)__builtin_ctz(f);
+    if (q > low) break;
+    f &= f - 1;
+    low++;
+  }
+  pre.tm_shift = low;
+  pre.tm_hi = f;
+  const int G = pairs_groups(op.k);
+  for (int hh = 0; hh < G; hh++) pre.dh[hh] = h_swb(h_ins0_mask((uint32_t)hh << low, f));
+  for (int it = 0; it < 4; it++) pre.tc[it] = h_swb(h_ins0_mask((uint32_t)(it * G) << low, f));
+}
+
+static bool build_inline(const TilePass &p, const HostPass &h, TileInline &I, int threads) {
   if (p.nops > kInlOps) return false;
   I.nops = (uint32_t)p.nops;
   I.nmat = 0;
@@ -230,6 +266,7 @@ static bool build_inline(const TilePass &p, const HostPass &h, TileInline &I) {
       op.mat = at;
       op.gen = kGenInline;
       I.nmat = at + cnt;
+      fill_pre(op, threads, I.pre[i]);
     }
     I.ops[i] = op;
   }
@@ -357,7 +394,7 @@ sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStr
   dim3 grid((unsigned)(1ull << (p.n - p.m)), (unsigned)batch);
   const int threads = tile_threads(p.m, s->dt);
   TileInline inl;   // copied into the launch
-  if (host && s->dt == SV_C64 && batch == 1 && p.nvec == 1 && build_inline(p, *host, inl))
+  if (host && s->dt == SV_C64 && batch == 1 && p.nvec == 1 && build_inline(p, *host, inl, threads))
     k_tile_inl<<<grid, threads, smem, stream>>>(p, inl);
   else if (s->dt == SV_C64)
     k_tile<float><<<grid, threads, smem, stream>>>(p);

@@ -77,9 +77,22 @@ constexpr uint8_t kGenInline = 0x40;     // TileOp.gen flag: matrix in the launc
 // do not fit keep the global copies.
 constexpr int kInlOps = 48;
 constexpr int kInlMat = 3200;    // complex64 entries
+// groups per trip of the packed complex64 blocks from the parameter block
+constexpr int pairs_groups(int k) { return k <= 2 ? 4 : 2; }
+// Per-op set-up of a parameter-block dense block, computed on the host for
+// the launch's thread count: the swizzled member offsets, the swizzled trip
+// offsets of the first trips and of a trip's groups, and the trip map.
+struct OpPre {
+  uint32_t soff[8];    // swb of the member offsets (the K target bits)
+  uint32_t dh[4];      // swb(l(h T)), h < groups per trip
+  uint32_t tc[4];      // swb(l(c0 T)) for the first four trips c0 = 0, G, 2G, 3G
+  uint32_t tm_hi;      // TripMap
+  uint32_t tm_shift;
+};
 struct TileInline {
   uint32_t nops, nmat;
   TileOp ops[kInlOps];
+  OpPre pre[kInlOps];
   float2 mats[kInlMat];
 };
 // TilePass.flags: this entry is not a tile pass but one 5-qubit dense block on

@@ -234,8 +234,10 @@ __device__ __forceinline__ uint64_t lds_b64(uint32_t a) {
 // datapath) or from global memory through L1, with the same arithmetic, so
 // every kernel that applies these blocks produces the same bits.
 struct ParamPairs {
+  static constexpr bool kPre = true;   // set-up from the host (OpPre)
   const TileInline &I;
   uint32_t base;
+  uint32_t oi;
   template <int D>
   __device__ __forceinline__ void pair(int p, int y, uint64_t &ur, uint64_t &ui) const {
     const uint64_t *M = reinterpret_cast<const uint64_t *>(&I.mats[base]);
@@ -244,6 +246,7 @@ struct ParamPairs {
   }
 };
 struct GlobalPairs {
+  static constexpr bool kPre = false;
   const float2 *U;   // row pairs, 16-byte aligned
   template <int D>
   __device__ __forceinline__ void pair(int p, int y, uint64_t &ur, uint64_t &ui) const {
@@ -257,14 +260,19 @@ __device__ __forceinline__ void dense_pairs(float2 *__restrict__ v, int m, const
   constexpr int D = 1 << K, NP = D / 2;
   const uint32_t vs = smem_u32(v);
   uint32_t soff[D], tmask = 0;
-  soff[0] = 0;
 #pragma unroll
-  for (int j = 0; j < K; j++) {
-    const uint32_t bit = 1u << op.t[j];
-    tmask |= bit;
-    const uint32_t e = swb<float>(bit);
+  for (int j = 0; j < K; j++) tmask |= 1u << op.t[j];
+  if constexpr (Src::kPre) {
 #pragma unroll
-    for (int y = 0; y < (1 << j); y++) soff[y + (1 << j)] = soff[y] ^ e;
+    for (int y = 0; y < D; y++) soff[y] = src.I.pre[src.oi].soff[y];
+  } else {
+    soff[0] = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+      const uint32_t e = swb<float>(1u << op.t[j]);
+#pragma unroll
+      for (int y = 0; y < (1 << j); y++) soff[y + (1 << j)] = soff[y] ^ e;
+    }
   }
   const uint32_t fixed = tmask | op.lcmask;
   const uint32_t ngroups = 1u << (m - __popc(fixed));
@@ -274,14 +282,25 @@ __device__ __forceinline__ void dense_pairs(float2 *__restrict__ v, int m, const
   // slot(c T), and a trip's G groups c0 + h share slot(c0 T)
   const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
   const uint32_t sthr = swb<float>(thread_l(threadIdx.x, op) | op.lcmask);
-  const TripMap tm = trip_map(T, fixed);
+  TripMap tm;
   uint32_t dh[G];
+  if constexpr (Src::kPre) {
+    const OpPre &pre = src.I.pre[src.oi];
+    tm = TripMap{pre.tm_shift, pre.tm_hi};
 #pragma unroll
-  for (int h = 0; h < G; h++) dh[h] = swb<float>(trip_l(h, tm));
-  for (uint32_t c0 = 0; c0 < ntrips; c0 += G) {
+    for (int h = 0; h < G; h++) dh[h] = pre.dh[h];
+  } else {
+    tm = trip_map(T, fixed);
+#pragma unroll
+    for (int h = 0; h < G; h++) dh[h] = swb<float>(trip_l(h, tm));
+  }
+  for (uint32_t c0 = 0, it = 0; c0 < ntrips; c0 += G, it++) {
     uint32_t s[G];
     bool ok[G];
-    const uint32_t sc = sthr ^ swb<float>(trip_l(c0, tm));
+    uint32_t sct;
+    if constexpr (Src::kPre) sct = it < 4 ? src.I.pre[src.oi].tc[it] : swb<float>(trip_l(c0, tm));
+    else sct = swb<float>(trip_l(c0, tm));
+    const uint32_t sc = sthr ^ sct;
 #pragma unroll
     for (int h = 0; h < G; h++) {
       ok[h] = c0 + h < ntrips;
@@ -329,7 +348,7 @@ __device__ __forceinline__ void dense_pairs(float2 *__restrict__ v, int m, const
 // groups per trip of the packed blocks (registers: three packed
 // accumulators per row pair and group); the grouping does not change the
 // arithmetic
-template <int K> constexpr int kPairsG = K <= 2 ? 4 : 2;
+template <int K> constexpr int kPairsG = pairs_groups(K);
 
 // groups per trip with matrices in global memory (batched, two-vector and
 // tensor-core passes, ops beyond a parameter block): the loaded pairs take
@@ -350,8 +369,8 @@ __device__ __forceinline__ void dense_pairs_global(float2 *v, int m, const TileO
 
 // Dense complex64 block of 1-3 qubits whose matrix is in the launch's
 // parameter block (op.mat indexes TileInline::mats, stored as row pairs).
-__device__ __forceinline__ void apply_op_inl(float2 *v, int m, const TileOp &op, const TileInline &I) {
-  const ParamPairs src{I, op.mat};
+__device__ __forceinline__ void apply_op_inl(float2 *v, int m, const TileOp &op, const TileInline &I, int oi) {
+  const ParamPairs src{I, op.mat, (uint32_t)oi};
   switch (op.k) {
     case 1: dense_pairs<1, kPairsG<1>>(v, m, op, src); break;
     case 2: dense_pairs<2, kPairsG<2>>(v, m, op, src); break;
