@@ -156,7 +156,9 @@ sv_status sv_set_basis(sv_state *s, uint64_t index);
 sv_status sv_upload(sv_state *s, const void *host, size_t bytes);
 sv_status sv_download(sv_state *s, void *host, size_t bytes);
 /* Wait for all work enqueued on the state's stream; reports device-side
- * timeouts raised by earlier calls. */
+ * errors raised by earlier calls: SV_ETIMEOUT when a bounded wait ran out,
+ * SV_EUNSUPPORTED when a tile pass met a block its launch did not carry (an
+ * internal invariant; the block was not applied).  Clears them. */
 sv_status sv_synchronize(sv_state *s);
 
 /* ---------------------------------------------------------------------------
