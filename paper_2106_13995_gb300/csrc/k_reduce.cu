@@ -8,6 +8,7 @@
 // FP64, so the chosen index is the one an FP64 reference would pick from the
 // same amplitudes (up to draws within ~1e-12 of a chunk boundary).
 #include <algorithm>
+#include <vector>
 
 #include "sv_device.cuh"
 #include "sv_internal.h"
@@ -234,9 +235,149 @@ __global__ void __launch_bounds__(kRedThreads) k_expect(const typename Cx<R>::T 
   block_sum_to(acc, partial + blockIdx.x);
 }
 
+// ---- diagonal groups (x mask 0) ---------------------------------------------
+// E = sum_x |psi_x|^2 f(x), f(x) = sum_t c_t (-1)^{popcount(x & z_t)} (real c_t:
+// the imaginary parts cancel for a diagonal group).  A warp sweeps chunks of
+// 32 lanes x kDiagTrips 16-byte units; index bits below LB + 5 + log2(trips)
+// (unit, lane and trip bits) vary inside a chunk, the bits above are fixed.
+// With x = h + l and z_t = (high part, low part L_t):
+//   chunk sum = sum_t c_t (-1)^{popcount(h & z_t)} P(L_t),
+//   P(L) = sum_l |psi_{h+l}|^2 (-1)^{popcount(l & L)},
+// a Walsh coefficient of the chunk's probabilities.  Each lane transforms
+// its 2^LB x trips probabilities over the unit and trip bits (the pattern
+// bits) in registers and parks the coefficients in shared memory; P(L) is
+// the sum over lanes of the lane's coefficient for L's pattern with the sign
+// of L's lane bits, so each lane accumulates its signed coefficients and
+// the block sums once at the end.  Terms sharing a low part form a group
+// whose chunk coefficient sums their high-part signs.  The group loop reads
+// the coefficients from shared memory, which keeps the code small (unrolled
+// over all patterns it missed the instruction cache).
+constexpr int kDiagTrips = 32;
+template <typename R> struct DiagArgs {
+  uint32_t ng;                              // groups (terms sharing a low part)
+  uint32_t gpat[kMaxGroupTerms];            // each group's pattern (unit and trip bits)
+  uint32_t lm[kMaxGroupTerms];              // each group's lane mask
+  uint32_t tstart[kMaxGroupTerms + 1];      // terms of each group
+  uint64_t zm[kMaxGroupTerms];              // terms, ordered by group
+  R c[kMaxGroupTerms];
+};
+constexpr int kDiagThreads = 128;
+
+template <typename R>
+__global__ void __launch_bounds__(kDiagThreads) k_expect_diag(const int4 *__restrict__ a, uint64_t nchunks,
+                                                              const __grid_constant__ DiagArgs<R> A,
+                                                              double *partial) {
+  using C = typename Cx<R>::T;
+  constexpr int APU = 16 / sizeof(C);
+  constexpr int TRIPS = kDiagTrips;
+  constexpr int NPAT = APU * TRIPS;
+  __shared__ R sq[kDiagThreads / 32][NPAT][32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  double acc = 0;
+  for (uint64_t ch = warp; ch < nchunks; ch += nwarps) {
+    const uint64_t ubase = ch * (32 * TRIPS);
+    const uint64_t x0 = ubase * APU;
+    R q[NPAT];
+#pragma unroll
+    for (int j = 0; j < TRIPS; j++) {
+      int4 raw = __ldcs(a + ubase + j * 32 + lane);
+      const C *v = reinterpret_cast<const C *>(&raw);
+#pragma unroll
+      for (int e = 0; e < APU; e++) q[e + APU * j] = v[e].x * v[e].x + v[e].y * v[e].y;
+    }
+#pragma unroll
+    for (int st = 1; st < NPAT; st <<= 1)
+#pragma unroll
+      for (int i = 0; i < NPAT; i++)
+        if (!(i & st)) {
+          const R u = q[i], w = q[i | st];
+          q[i] = u + w;
+          q[i | st] = u - w;
+        }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < NPAT; i++) sq[wi][i][lane] = q[i];
+    __syncwarp();
+    R part = 0;
+    for (uint32_t g = 0; g < A.ng; g++) {
+      R ck = 0;
+      for (uint32_t t = A.tstart[g]; t < A.tstart[g + 1]; t++)
+        ck += (__popcll(x0 & A.zm[t]) & 1) ? -A.c[t] : A.c[t];
+      const R qv = sq[wi][A.gpat[g]][lane];
+      part += (__popc((uint32_t)lane & A.lm[g]) & 1) ? -ck * qv : ck * qv;
+    }
+    acc += (double)part;
+  }
+  block_sum_to(acc, partial + blockIdx.x);
+}
+
+// Launch the diagonal kernel for a group of Z strings; false (nothing
+// launched) when the state is smaller than one chunk.
+template <typename R>
+static bool expect_diag_launch(sv_state *s, const uint64_t *zm, const double *cf, const int *ipow, int nt,
+                               double *out_dev, sv_status &st) {
+  constexpr int APU = 16 / (2 * (int)sizeof(R));
+  constexpr int LB = APU == 2 ? 1 : 0;
+  constexpr int TB = 5;   // log2(kDiagTrips)
+  constexpr int NPAT = APU * kDiagTrips;
+  if (s->n < LB + 5 + TB) return false;
+  struct T {
+    int pat;
+    uint32_t lm;
+    uint64_t z;
+    double c;
+  };
+  std::vector<T> ts;
+  for (int t = 0; t < nt; t++) {
+    const uint64_t lo = zm[t] & ((1ull << (LB + 5 + TB)) - 1);
+    const int pat = (int)((lo & ((1u << LB) - 1)) | (((lo >> (LB + 5)) & (kDiagTrips - 1)) << LB));
+    const uint32_t lm = (uint32_t)((lo >> LB) & 31);
+    const double c = (ipow[t] & 2) ? -cf[t] : cf[t];   // i^k, k even
+    ts.push_back({pat, lm, zm[t], c});
+  }
+  std::stable_sort(ts.begin(), ts.end(), [](const T &x, const T &y) {
+    return x.pat != y.pat ? x.pat < y.pat : x.lm < y.lm;
+  });
+  DiagArgs<R> A{};
+  int ng = 0;
+  for (int t = 0; t < nt; t++) {
+    if (t == 0 || ts[t].pat != ts[t - 1].pat || ts[t].lm != ts[t - 1].lm) {
+      A.gpat[ng] = (uint32_t)ts[t].pat;
+      A.lm[ng] = ts[t].lm;
+      A.tstart[ng] = (uint32_t)t;
+      ng++;
+    }
+    A.zm[t] = ts[t].z;
+    A.c[t] = (R)ts[t].c;
+  }
+  A.tstart[ng] = (uint32_t)nt;
+  A.ng = (uint32_t)ng;
+  (void)NPAT;
+  const uint64_t nchunks = (1ull << s->n) / ((uint64_t)APU * 32 * kDiagTrips);
+  double *partial = reinterpret_cast<double *>(s->ws + kWsRed);
+  // a warp per chunk, up to eight blocks per SM (the partial-sum area holds them)
+  const uint64_t want = (nchunks * 32 + kDiagThreads - 1) / kDiagThreads;
+  const int g = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)s->sm_count * 8));
+  k_expect_diag<R><<<g, kDiagThreads, 0, s->stream>>>(reinterpret_cast<const int4 *>(s->amps), nchunks, A,
+                                                       partial);
+  k_finalize<<<1, 32, 0, s->stream>>>(partial, g, 1, out_dev);
+  g_launches += 2;
+  const cudaError_t e = cudaGetLastError();
+  st = e == cudaSuccess ? SV_OK : cuda_error(e, "k_expect_diag");
+  return true;
+}
+
 template <typename R>
 static sv_status expect_launch(sv_state *s, uint64_t xm, const uint64_t *zm, const double *cf, const int *ipow,
                                int nt, double *out_dev) {
+  if (xm == 0) {
+    bool odd = false;   // an odd power of i would make a term imaginary
+    for (int t = 0; t < nt; t++) odd |= (ipow[t] & 1) != 0;
+    sv_status st = SV_OK;
+    if (!odd && expect_diag_launch<R>(s, zm, cf, ipow, nt, out_dev, st)) return st;
+  }
   ExpectArgs<R> A{};
   A.xm = xm;
   A.nt = nt;
