@@ -637,29 +637,64 @@ __global__ void k_chunk_sums(const typename Cx<R>::T *__restrict__ a, int n, uin
   }
 }
 
-// in-place inclusive prefix sum over nchunks doubles, one block of 1024
-__global__ void k_scan(double *x, uint64_t len) {
-  __shared__ double tot[1024];
-  const uint64_t per = (len + blockDim.x - 1) / blockDim.x;
-  const uint64_t lo = threadIdx.x * per, hi = lo + per < len ? lo + per : len;
-  double s = 0;
-  for (uint64_t i = lo; i < hi; i++) s += x[i];
-  tot[threadIdx.x] = s;
+// Inclusive FP64 prefix sums of the chunk totals, coalesced: k_scan_seg
+// scans segments of kScanSeg values in place (warp shuffles, then the warps'
+// totals) and writes each segment's total; the totals are scanned the same
+// way, level by level, and k_scan_add adds segment b's offset (the scanned
+// total of segments 0..b-1) to its values.
+constexpr int kScanSeg = 1024;
+__global__ void __launch_bounds__(kScanSeg) k_scan_seg(double *x, uint64_t len, double *tops) {
+  __shared__ double wsum[kScanSeg / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t i = (uint64_t)blockIdx.x * kScanSeg + threadIdx.x;
+  double v = i < len ? x[i] : 0.0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) wsum[w] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = 0;
-    for (unsigned t = 0; t < blockDim.x; t++) {
-      const double v = tot[t];
-      tot[t] = r;
-      r += v;
+  if (w == 0) {
+    double t = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
     }
+    wsum[lane] = t;
   }
   __syncthreads();
-  double r = tot[threadIdx.x];
-  for (uint64_t i = lo; i < hi; i++) {
-    r += x[i];
-    x[i] = r;
+  if (w > 0) v += wsum[w - 1];
+  if (i < len) x[i] = v;
+  if (tops && threadIdx.x == kScanSeg - 1) tops[blockIdx.x] = v;
+}
+__global__ void __launch_bounds__(kScanSeg) k_scan_add(double *x, uint64_t len, const double *tops) {
+  const uint64_t b = (uint64_t)blockIdx.x + 1;   // segment 0 has no offset
+  const uint64_t i = b * kScanSeg + threadIdx.x;
+  if (i < len) x[i] += tops[b - 1];
+}
+// scan x[0, len); tops: scratch for the segment totals of every level
+static void scan_levels(double *x, uint64_t len, double *tops, cudaStream_t st) {
+  if (len <= (uint64_t)kScanSeg) {
+    k_scan_seg<<<1, kScanSeg, 0, st>>>(x, len, nullptr);
+    g_launches++;
+    return;
   }
+  const uint64_t nseg = (len + kScanSeg - 1) / kScanSeg;
+  k_scan_seg<<<(unsigned)nseg, kScanSeg, 0, st>>>(x, len, tops);
+  scan_levels(tops, nseg, tops + ((nseg + 31) & ~(uint64_t)31), st);
+  k_scan_add<<<(unsigned)(nseg - 1), kScanSeg, 0, st>>>(x, len, tops);
+  g_launches += 2;
+}
+size_t scan_scratch_bytes(int n) {
+  const int cb = n < 10 ? n : 10;
+  uint64_t len = 1ull << (n - cb), total = 0;
+  while (len > (uint64_t)kScanSeg) {
+    len = (len + kScanSeg - 1) / kScanSeg;
+    total += (len + 31) & ~(uint64_t)31;
+  }
+  return (size_t)total * sizeof(double);
 }
 
 // one warp per shot: binary search over chunk prefixes, then a warp scan
@@ -715,8 +750,12 @@ sv_status launch_sample_prepare(sv_state *s) {
     k_chunk_sums<float><<<g, kRedThreads, 0, s->stream>>>((const float2 *)s->amps, s->n, nchunks, csum);
   else
     k_chunk_sums<double><<<g, kRedThreads, 0, s->stream>>>((const double2 *)s->amps, s->n, nchunks, csum);
-  k_scan<<<1, 1024, 0, s->stream>>>(csum, nchunks);
-  g_launches += 2;
+  g_launches++;
+  // the scan's scratch follows the shot buffer
+  scan_levels(csum, nchunks,
+              reinterpret_cast<double *>(s->ws + kWsRed + sample_shot_offset(s->n) +
+                                         sample_shot_capacity() * sizeof(uint64_t)),
+              s->stream);
   SV_CUDA(cudaGetLastError());
   return SV_OK;
 }

@@ -33,7 +33,8 @@ int mmax(sv_dtype dt, int nvec) {
 size_t red_bytes(int n) {
   const int cb = n < 10 ? n : 10;
   const size_t chunks = (size_t)1 << (n - cb);
-  size_t need = chunks * sizeof(double) + (1 << 20);  // CDF chunks + shot buffer
+  // CDF chunks (256-byte aligned) + shot buffer + the prefix scan's scratch
+  size_t need = ((chunks * sizeof(double) + 255) & ~(size_t)255) + (1 << 20) + scan_scratch_bytes(n);
   return std::max<size_t>(need, 2 << 20);
 }
 

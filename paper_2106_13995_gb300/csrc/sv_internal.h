@@ -318,6 +318,7 @@ sv_status zall_noalloc(const void *amps, int n, sv_dtype dt, double *out, cudaSt
 sv_status launch_sample_prepare(sv_state *s);
 sv_status launch_sample_shots(sv_state *s, int64_t shot0, int64_t count, uint64_t seed, uint64_t *out_dev);
 size_t sample_shot_offset(int n);
+size_t scan_scratch_bytes(int n);   // prefix-scan scratch after the shot buffer
 int64_t sample_shot_capacity();
 sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch);
 // Append a complex64 dense matrix of k <= 3 qubits (row-major U) to a pool

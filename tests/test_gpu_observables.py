@@ -63,7 +63,8 @@ def test_z_all_large(svlib, oracle):
 @pytest.mark.parametrize("dt", ["c64", "c128"])
 def test_sample_matches_oracle(svlib, oracle, dt):
     rng = np.random.default_rng(3)
-    for n in (4, 11, 16):
+    # 21 and 22 qubits: 2048 and 4096 CDF chunks, a two-level prefix scan
+    for n in (4, 11, 16, 21, 22):
         s = svlib.StateVector(n, dt).load(W.random_state(n, rng))
         cast = s.numpy().astype(np.complex128)
         shots, seed = 20000, 12345 + n
