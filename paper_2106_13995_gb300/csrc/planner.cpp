@@ -210,4 +210,46 @@ std::vector<PassPlan> plan_passes(const std::vector<Block> &blocks, int n, int m
   return passes;
 }
 
+// Merge small blocks inside each pass: a block joins an earlier block of the
+// same pass when every block between them acts on other qubits (so it may
+// move back next to it) and the two together touch at most K qubits.  The
+// product is formed in FP64 as in fuse().  Blocks with controls, parameters
+// or non-dense kinds neither merge nor move past blocks sharing a qubit.
+static bool mergeable(const Block &b) {
+  return b.kind == TOP_DENSE && b.controls.empty() && b.param < 0 && b.inst < 0 && b.fusable;
+}
+std::vector<Block> merge_in_passes(const std::vector<PassPlan> &passes, int K) {
+  std::vector<Block> out;
+  for (const PassPlan &P : passes) {
+    std::vector<Block> ops = P.ops;
+    std::vector<char> alive(ops.size(), 1);
+    for (size_t j = 0; j < ops.size(); j++) {
+      if (!mergeable(ops[j])) continue;
+      const uint64_t tj = qmask(ops[j].qubits);
+      for (size_t i = j; i-- > 0;) {
+        if (!alive[i]) continue;
+        const uint64_t ti = qmask(ops[i].qubits) | qmask(ops[i].controls) | ops[i].xmask;
+        if (mergeable(ops[i]) && __builtin_popcountll(qmask(ops[i].qubits) | tj) <= K) {
+          Block &A = ops[i];
+          std::vector<int> uni = A.qubits;
+          for (int q : ops[j].qubits)
+            if (index_of(uni, q) < 0) uni.push_back(q);
+          const int D = 1 << (int)uni.size();
+          const std::vector<cd> Ua = embed(A.U, A.qubits, {}, uni);
+          const std::vector<cd> Ub = embed(ops[j].U, ops[j].qubits, {}, uni);
+          A.U = matmul(Ub, Ua, D);   // ops[j] acts after ops[i]
+          A.qubits = uni;
+          A.diag = is_diagonal(A.U, (int)uni.size());
+          alive[j] = 0;
+          break;
+        }
+        if (ti & tj) break;   // ops[j] cannot move past a block on its qubits
+      }
+    }
+    for (size_t k = 0; k < ops.size(); k++)
+      if (alive[k]) out.push_back(std::move(ops[k]));
+  }
+  return out;
+}
+
 }  // namespace sv

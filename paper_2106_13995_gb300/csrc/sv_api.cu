@@ -338,6 +338,19 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
   int m = o.tile_m, L = o.L;
   if (!fit_tile(out.blocks, s->n, lmin(s->dt), mmax(s->dt, 1), m, L))
     return set_error(SV_EUNSUPPORTED, "a fused block does not fit a shared-memory tile");
+  if (o.prec == SV_PREC_PLAIN && o.fusion_k >= 2 && m < s->n) {
+    // blocks that meet inside a pass merge (one pass-sized op instead of two)
+    const std::vector<PassPlan> first = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, kMaxMatPerPass);
+    if (!first.empty()) {
+      std::vector<Block> merged = merge_in_passes(first, o.fusion_k);
+      int m2 = m, L2 = L;
+      if (merged.size() < out.blocks.size() && fit_tile(merged, s->n, lmin(s->dt), mmax(s->dt, 1), m2, L2)) {
+        out.blocks = std::move(merged);
+        m = m2;
+        L = L2;
+      }
+    }
+  }
   BuildCtx b{s->dt, s->n, m, L, 1, 0, o.prec};
   // With a tensor-core precision mode, dense 5-qubit blocks run on the tensor
   // cores: inside 12-qubit tile passes (TOP_TC ops) when the tile size is

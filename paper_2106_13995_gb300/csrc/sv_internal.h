@@ -198,6 +198,9 @@ bool fit_tile(const std::vector<Block> &blocks, int n, int lmin, int mmax, int &
 // qubits (callers size m and L with fit_tile first).
 std::vector<PassPlan> plan_passes(const std::vector<Block> &blocks, int n, int m, int L,
                                   int max_ops, int max_mat_entries);
+// Blocks of the planned passes in execution order, with blocks of a pass
+// merged where commuting lets them meet and the union has at most K qubits.
+std::vector<Block> merge_in_passes(const std::vector<PassPlan> &passes, int K);
 
 // ---------------------------------------------------------------------------
 // state handle

@@ -29,7 +29,8 @@ static uint32_t ins0_mask_h(uint32_t x, uint32_t f) {
 }
 
 // returns the number of passes, or -1 (message printed)
-extern "C" int plan_emulate(const sv_circuit *c, double *psi_, int fusion_k, int m, int L, int *n_blocks) {
+extern "C" int plan_emulate(const sv_circuit *c, double *psi_, int fusion_k, int m, int L, int *n_blocks,
+                            int merge) {
   std::vector<Gate> gates;
   if (circuit_to_gates(c, nullptr, c->n_qubits, gates, false) != SV_OK) {
     std::printf("circuit rejected: %s\n", sv_last_error());
@@ -43,6 +44,16 @@ extern "C" int plan_emulate(const sv_circuit *c, double *psi_, int fusion_k, int
     return -1;
   }
   std::vector<PassPlan> passes = plan_passes(blocks, n, m, L, 256, 1 << 16);
+  if (merge && fusion_k >= 2 && !passes.empty()) {
+    // the library's merging of blocks that meet inside a pass, then a new plan
+    blocks = merge_in_passes(passes, fusion_k);
+    if (n_blocks) *n_blocks = (int)blocks.size();
+    if (!fit_tile(blocks, n, 0, 16, m, L)) {
+      std::printf("merged blocks do not fit a tile\n");
+      return -1;
+    }
+    passes = plan_passes(blocks, n, m, L, 256, 1 << 16);
+  }
   if (passes.empty() && !blocks.empty()) {
     std::printf("planning failed\n");
     return -1;

@@ -33,17 +33,17 @@ def emu():
         subprocess.check_call([B.nvcc(), *B.ARCH, "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
                                "-I", os.path.join(ROOT, "include"), "-o", lib, src, *objs])
     L = C.CDLL(lib)
-    L.plan_emulate.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
+    L.plan_emulate.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
     return L
 
 
-def run(emu, circ, fk, m, L):
+def run(emu, circ, fk, m, L, merge=0):
     from paper_2106_13995_gb300 import sim
     mm = sim.marshal(circ)
     psi = np.zeros(1 << circ.n_qubits, dtype=np.complex128)
     psi[0] = 1
     nb = C.c_int()
-    npass = emu.plan_emulate(C.addressof(mm.c), psi.ctypes.data, fk, m, L, C.byref(nb))
+    npass = emu.plan_emulate(C.addressof(mm.c), psi.ctypes.data, fk, m, L, C.byref(nb), merge)
     assert npass > 0
     return psi, npass, nb.value
 
@@ -75,3 +75,26 @@ def test_fusion_reduces_blocks(emu):
     _, p3, b3 = run(emu, c, 3, 8, 3)
     assert b3 < b1 == len(c.ops)
     assert p1 > 0 and p3 > 0
+
+
+@pytest.mark.parametrize("fk", [2, 3, 4])
+def test_merge_in_passes_matches_oracle(emu, oracle, fk):
+    """Blocks of a pass that commuting lets meet merge into one block of at
+    most fk qubits; the merged program still reproduces the FP64 oracle, and
+    never has more blocks than the unmerged one."""
+    for seed in range(6):
+        n = 9 + seed % 3
+        c = W.random_gate_circuit(n, 80, seed=seed * 11 + fk)
+        want = oracle.run(c)
+        for m, L in ((n, 3), (7, 1), (8, 3)):
+            _, _, nb0 = run(emu, c, fk, m, L)
+            got, npass, nb = run(emu, c, fk, m, L, merge=1)
+            assert npass > 0
+            assert nb <= nb0
+            assert oracle.infidelity(want, got) <= 1e-12, (seed, m, L)
+    g = W.grid_random(4, 4, 10, 2)
+    want = oracle.run(g)
+    _, _, nb0 = run(emu, g, 3, 10, 3)
+    got, _, nb = run(emu, g, 3, 10, 3, merge=1)
+    assert nb < nb0
+    assert oracle.infidelity(want, got) <= 1e-12
