@@ -9,6 +9,7 @@
 // a GPU.
 #include <complex>
 #include <cstdio>
+#include <set>
 #include <vector>
 
 #include "../../paper_2106_13995_gb300/csrc/sv_internal.h"
@@ -123,4 +124,74 @@ extern "C" int plan_emulate(const sv_circuit *c, double *psi_, int fusion_k, int
     }
   }
   return (int)prog.passes.size();
+}
+
+// The complex64 program of a circuit, checked op by op against the device's
+// group enumeration: thread t's first group sits at l(t) = OR over bits i of t
+// of 1 << (TileOp.tbpos nibble i), trip c adds ins0_mask(c << shift, hi) with
+// the trip map of the thread count T (fixed positions up to the trip region
+// shift it, those above are inserted).  For T = the tile pass's thread count
+// and 512 (the persistent kernel) every op's groups must come out exactly
+// once.  Returns the number of ops checked, or -1 (message printed);
+// *spread counts ops whose lanes 0..15 reach 16 different bank rows of the
+// swizzled layout (slot l ^ ((l >> 4) & 15), modulo 16).
+extern "C" int check_thread_positions(const sv_circuit *c, int fusion_k, int m, int L, int *spread) {
+  std::vector<Gate> gates;
+  if (circuit_to_gates(c, nullptr, c->n_qubits, gates, false) != SV_OK) return -1;
+  const int n = c->n_qubits;
+  std::vector<Block> blocks = fuse(gates, fusion_k);
+  if (!fit_tile(blocks, n, 1, 14, m, L)) return -1;
+  std::vector<PassPlan> passes = plan_passes(blocks, n, m, L, 256, 1 << 16);
+  DeviceProgram prog;
+  std::vector<uint32_t> op0s;
+  BuildCtx bc{SV_C64, n, m, L, 1, 0};
+  for (const PassPlan &P : passes)
+    if (emit_pass(prog, P, bc, op0s, {}) != SV_OK) return -1;
+  int checked = 0, good = 0;
+  for (size_t pi = 0; pi < prog.passes.size(); pi++) {
+    const TilePass &tp = prog.passes[pi];
+    for (int oi = 0; oi < tp.nops; oi++) {
+      const TileOp &op = prog.ops[op0s[pi] + oi];
+      if (op.kind != TOP_DENSE && op.kind != TOP_DIAG) continue;
+      uint32_t fixed = op.lcmask;
+      if (op.kind == TOP_DENSE)
+        for (int j = 0; j < op.k; j++) fixed |= 1u << op.t[j];
+      const uint32_t ngroups = 1u << (tp.m - __builtin_popcount(fixed));
+      auto thread_l = [&](uint32_t t) {
+        uint32_t l = 0;
+        for (int i = 0; i < 9; i++) l |= ((t >> i) & 1u) << ((op.tbpos[i >> 1] >> (4 * (i & 1))) & 15u);
+        return l;
+      };
+      for (int T : {tile_threads(tp.m, SV_C64), 512}) {
+        uint32_t low = (uint32_t)__builtin_ctz((uint32_t)T), f = fixed;
+        while (f) {
+          const uint32_t q = (uint32_t)__builtin_ctz(f);
+          if (q > low) break;
+          f &= f - 1;
+          low++;
+        }
+        const uint32_t nthr = ngroups < (uint32_t)T ? ngroups : (uint32_t)T;
+        const uint32_t ntrips = ngroups > (uint32_t)T ? ngroups / (uint32_t)T : 1u;
+        std::multiset<uint32_t> got, want;
+        for (uint32_t t = 0; t < nthr; t++)
+          for (uint32_t cc = 0; cc < ntrips; cc++) got.insert(thread_l(t) ^ ins0_mask_h(cc << low, f));
+        for (uint32_t g = 0; g < ngroups; g++) want.insert(ins0_mask_h(g, fixed));
+        if (got != want) {
+          std::printf("pass %zu op %d (k %d, fixed %x, T %d): groups differ\n", pi, oi, op.k, fixed, T);
+          return -1;
+        }
+      }
+      if (ngroups >= 16) {
+        uint32_t rows = 0;
+        for (uint32_t t = 0; t < 16; t++) {
+          const uint32_t l = thread_l(t) | op.lcmask;
+          rows |= 1u << ((l ^ ((l >> 4) & 15u)) & 15u);
+        }
+        good += rows == 0xffffu;
+      }
+      checked++;
+    }
+  }
+  if (spread) *spread = good;
+  return checked;
 }

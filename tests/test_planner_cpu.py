@@ -34,6 +34,7 @@ def emu():
                                "-I", os.path.join(ROOT, "include"), "-o", lib, src, *objs])
     L = C.CDLL(lib)
     L.plan_emulate.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
+    L.check_thread_positions.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
     return L
 
 
@@ -98,3 +99,19 @@ def test_merge_in_passes_matches_oracle(emu, oracle, fk):
     got, _, nb = run(emu, g, 3, 10, 3, merge=1)
     assert nb < nb0
     assert oracle.infidelity(want, got) <= 1e-12
+
+
+def test_thread_positions_cover_every_group(emu):
+    """The plan-time thread-bit positions of complex64 tile ops: with the
+    trip map of the launch's thread count (and of the 512-thread persistent
+    kernel) every op visits each of its groups exactly once, and most ops'
+    16 lanes of a wavefront reach 16 bank rows."""
+    from paper_2106_13995_gb300 import sim
+    for c, fk, m in ((W.grid_random(4, 5, 10, 1), 3, 13), (W.grid_random(4, 4, 10, 2), 2, 12),
+                     (W.random_gate_circuit(14, 120, seed=5), 3, 12), (W.multiplier(3), 3, 10),
+                     (W.random_gate_circuit(12, 80, seed=9), 1, 9)):
+        mm = sim.marshal(c)
+        spread = C.c_int()
+        checked = emu.check_thread_positions(C.addressof(mm.c), fk, min(m, c.n_qubits), 3, C.byref(spread))
+        assert checked > 0, c.name
+        assert spread.value >= 0.5 * checked, (c.name, spread.value, checked)
