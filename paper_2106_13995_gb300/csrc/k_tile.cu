@@ -227,7 +227,7 @@ static uint32_t h_ins0_mask(uint32_t x, uint32_t fixed) {
   return x;
 }
 
-static void fill_pre(const TileOp &op, int threads, OpPre &pre) {
+void fill_op_pre(const TileOp &op, int threads, OpPre &pre) {
   std::memset(&pre, 0, sizeof(pre));
   uint32_t fixed = op.lcmask;
   pre.soff[0] = 0;
@@ -266,7 +266,7 @@ static bool build_inline(const TilePass &p, const HostPass &h, TileInline &I, in
       op.mat = at;
       op.gen = kGenInline;
       I.nmat = at + cnt;
-      fill_pre(op, threads, I.pre[i]);
+      fill_op_pre(op, threads, I.pre[i]);
     }
     I.ops[i] = op;
   }

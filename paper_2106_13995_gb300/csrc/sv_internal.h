@@ -89,6 +89,8 @@ struct OpPre {
   uint32_t tm_hi;      // TripMap
   uint32_t tm_shift;
 };
+// OpPre of a 1-3 qubit dense op for a launch with `threads` threads (k_tile.cu)
+void fill_op_pre(const TileOp &op, int threads, OpPre &pre);
 struct TileInline {
   uint32_t nops, nmat;
   TileOp ops[kInlOps];

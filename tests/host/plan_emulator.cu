@@ -195,3 +195,62 @@ extern "C" int check_thread_positions(const sv_circuit *c, int fusion_k, int m, 
   if (spread) *spread = good;
   return checked;
 }
+
+// The host-computed set-up of parameter-block ops (OpPre), against slots
+// computed directly: for every dense 1-3 qubit op of the complex64 program,
+// thread t, trip it < 4, group h of the trip and member y, the device's
+// slot swb(l(t) | lcmask) ^ tc[it] ^ dh[h] ^ soff[y] must be the swizzled
+// byte offset of that amplitude (group base l(t) ^ trip part, plus the
+// member's target bits).  Returns the number of ops checked, or -1.
+extern "C" int check_op_pre(const sv_circuit *c, int m, int L) {
+  std::vector<Gate> gates;
+  if (circuit_to_gates(c, nullptr, c->n_qubits, gates, false) != SV_OK) return -1;
+  const int n = c->n_qubits;
+  std::vector<Block> blocks = fuse(gates, 3);
+  if (!fit_tile(blocks, n, 1, 14, m, L)) return -1;
+  std::vector<PassPlan> passes = plan_passes(blocks, n, m, L, 256, 1 << 16);
+  DeviceProgram prog;
+  std::vector<uint32_t> op0s;
+  BuildCtx bc{SV_C64, n, m, L, 1, 0};
+  for (const PassPlan &P : passes)
+    if (emit_pass(prog, P, bc, op0s, {}) != SV_OK) return -1;
+  auto swb = [](uint32_t l) { return (l ^ ((l >> 4) & 15u)) * 8u; };
+  int checked = 0;
+  for (size_t pi = 0; pi < prog.passes.size(); pi++) {
+    const TilePass &tp = prog.passes[pi];
+    const int T = tile_threads(tp.m, SV_C64);
+    for (int oi = 0; oi < tp.nops; oi++) {
+      const TileOp &op = prog.ops[op0s[pi] + oi];
+      if (op.kind != TOP_DENSE || op.k > 3) continue;
+      OpPre pre;
+      fill_op_pre(op, T, pre);
+      uint32_t fixed = op.lcmask;
+      for (int j = 0; j < op.k; j++) fixed |= 1u << op.t[j];
+      const uint32_t ngroups = 1u << (tp.m - __builtin_popcount(fixed));
+      const uint32_t ntrips = ngroups > (uint32_t)T ? ngroups / (uint32_t)T : 1u;
+      const int G = pairs_groups(op.k);
+      const uint32_t nthr = ngroups < (uint32_t)T ? ngroups : (uint32_t)T;
+      for (uint32_t t = 0; t < nthr; t++) {
+        uint32_t lt = 0;
+        for (int i = 0; i < 9; i++) lt |= ((t >> i) & 1u) << ((op.tbpos[i >> 1] >> (4 * (i & 1))) & 15u);
+        for (uint32_t it = 0; it < 4 && it * (uint32_t)G < ntrips; it++)
+          for (int h = 0; h < G && it * G + h < ntrips; h++) {
+            const uint32_t cc = it * G + h;
+            const uint32_t lg = lt ^ ins0_mask_h(cc * (uint32_t)T, fixed);   // the group's base index
+            for (int y = 0; y < (1 << op.k); y++) {
+              uint32_t off = 0;
+              for (int j = 0; j < op.k; j++) off |= (uint32_t)((y >> j) & 1) << op.t[j];
+              const uint32_t want = swb(lg | op.lcmask | off);
+              const uint32_t got = swb(lt | op.lcmask) ^ pre.tc[it] ^ pre.dh[h] ^ pre.soff[y];
+              if (got != want) {
+                std::printf("pass %zu op %d t %u trip %u h %d y %d: %x != %x\n", pi, oi, t, it, h, y, got, want);
+                return -1;
+              }
+            }
+          }
+      }
+      checked++;
+    }
+  }
+  return checked;
+}

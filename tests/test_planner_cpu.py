@@ -35,6 +35,7 @@ def emu():
     L = C.CDLL(lib)
     L.plan_emulate.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int]
     L.check_thread_positions.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
+    L.check_op_pre.argtypes = [C.c_void_p, C.c_int, C.c_int]
     return L
 
 
@@ -115,3 +116,15 @@ def test_thread_positions_cover_every_group(emu):
         checked = emu.check_thread_positions(C.addressof(mm.c), fk, min(m, c.n_qubits), 3, C.byref(spread))
         assert checked > 0, c.name
         assert spread.value >= 0.5 * checked, (c.name, spread.value, checked)
+
+
+def test_op_setup_records_match_direct_slots(emu):
+    """The per-op set-up the host puts in a tile pass's parameter block
+    (member offsets, trip map, offsets of a trip's groups and of the first
+    four trips) composes to the swizzled slot of every amplitude the op
+    touches in those trips."""
+    from paper_2106_13995_gb300 import sim
+    for c, m in ((W.grid_random(4, 5, 10, 1), 13), (W.random_gate_circuit(14, 120, seed=5), 12),
+                 (W.random_gate_circuit(11, 60, seed=2), 9), (W.multiplier(3), 10)):
+        mm = sim.marshal(c)
+        assert emu.check_op_pre(C.addressof(mm.c), min(m, c.n_qubits), 3) > 0, c.name
