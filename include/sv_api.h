@@ -249,7 +249,8 @@ sv_status sv_expect_z_all(sv_state *s, double *out_host);
  * make it before any stream capture.  All calls share the array: calls whose
  * work overlaps on the GPU (different streams, or different host threads)
  * race and give wrong results; serialise them.
- * Errors: SV_EINVAL for null or misaligned pointers, an unknown dtype, or
+ * Errors: SV_EINVAL for null or misaligned pointers, pointers that are not
+ * device (or managed) memory of the current device, an unknown dtype, or
  * n_qubits outside [1, 34] (the array's limit); SV_ECUDA if the runtime
  * cannot resolve the array or launch. */
 sv_status sv_expect_z_all_noalloc(const void *amps_dev, int n_qubits, sv_dtype dtype, double *out_dev,
@@ -319,6 +320,15 @@ sv_status sv_wait_selftest(void *stream, uint64_t polls);
 /* Number of kernels this library has launched in this process (all
  * devices).  Lets callers count device work without a profiler. */
 uint64_t sv_kernel_launch_count(void);
+
+/* Bound on the number of planned circuit programs the library keeps in host
+ * memory (all state handles together; default 2048).  A program is cached
+ * per (state, circuit, parameters, options) so repeated sv_apply_circuit
+ * calls skip fusion and planning; beyond the bound the oldest entries are
+ * dropped (a call that is using an entry keeps it alive until it returns).
+ * max_programs <= 0 only queries.  Returns the previous bound.  Thread-safe.
+ * The paper has no counterpart: this is a service of this library. */
+int64_t sv_program_cache_limit(int64_t max_programs);
 
 const char *sv_last_error(void);
 const char *sv_status_string(sv_status st);

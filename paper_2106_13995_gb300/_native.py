@@ -98,6 +98,7 @@ def lib():
             "sv_autotune": (st, [vp, C.POINTER(SvCircuit), C.POINTER(SvOptions)]),
             "sv_wait_selftest": (st, [vp, C.c_uint64]),
             "sv_kernel_launch_count": (C.c_uint64, []),
+            "sv_program_cache_limit": (C.c_int64, [C.c_int64]),
             "sv_last_error": (C.c_char_p, []),
             "sv_status_string": (C.c_char_p, [C.c_int]),
         }

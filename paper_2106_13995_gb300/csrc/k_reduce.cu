@@ -8,6 +8,7 @@
 // FP64, so the chosen index is the one an FP64 reference would pick from the
 // same amplitudes (up to draws within ~1e-12 of a chunk boundary).
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "sv_device.cuh"
@@ -545,22 +546,35 @@ sv_status launch_z_all(sv_state *s, double *out_dev) {
 constexpr int kNoAllocBlocks = 512;
 constexpr int kNoAllocMaxQ = 34;
 static __device__ __align__(256) double g_zall_scratch[kNoAllocBlocks * (kNoAllocMaxQ + 1)];
-static double *g_zall_scratch_addr[64];   // device address of the array, per device
+struct NoAllocDev {
+  double *scratch = nullptr;   // device address of g_zall_scratch on this device
+  int sms = 0;
+};
+static NoAllocDev g_noalloc_dev[64];
+static std::mutex g_noalloc_mu;
 
 sv_status zall_noalloc(const void *amps, int n, sv_dtype dt, double *out, cudaStream_t stream) {
   int dev = 0;
   SV_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return set_error(SV_EUNSUPPORTED, "device ordinal above 63");
-  if (!g_zall_scratch_addr[dev]) {
-    // the array's name is only a host-side handle: ask the runtime for its
-    // address on the current device, once per device
-    void *p = nullptr;
-    SV_CUDA(cudaGetSymbolAddress(&p, g_zall_scratch));
-    g_zall_scratch_addr[dev] = static_cast<double *>(p);
+  NoAllocDev d;
+  {
+    // once per device, under a lock (host threads may call concurrently):
+    // the array's name is only a host-side handle, so ask the runtime for
+    // its address on the current device; the SM count sizes the grid
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_dev[dev].scratch) {
+      void *p = nullptr;
+      int sms = 0;
+      SV_CUDA(cudaGetSymbolAddress(&p, g_zall_scratch));
+      SV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      g_noalloc_dev[dev].sms = sms;
+      g_noalloc_dev[dev].scratch = static_cast<double *>(p);
+    }
+    d = g_noalloc_dev[dev];
   }
-  double *partial = g_zall_scratch_addr[dev];
-  int sms = 0;
-  SV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double *partial = d.scratch;
+  const int sms = d.sms;
   const int apu = dt == SV_C64 ? 2 : 1;
   const uint64_t namps = 1ull << n;
   const uint64_t chunk_amps = 32ull * 8 * apu;

@@ -256,11 +256,7 @@ sv_status launch_dense_tc(sv_state *s, void *amps, const int *targets, const uin
   A.err = reinterpret_cast<uint32_t *>(s->ws + kWsCtrl + kWsErrFlag);
   A.mode = mode == SV_PREC_TC_TF32X3 ? 1u : 2u;
   A.spin_limit = (uint32_t)std::min<uint64_t>(spin_limit ? spin_limit : (1u << 22), 0xFFFFFFFFu);
-  static bool attr = false;
-  if (!attr) {
-    SV_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal));
-    attr = true;
-  }
+  SV_TRY(func_attr_once((const void *)k_dense_tc, s->device, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal));
   const uint64_t ntiles = A.ngroups / kTcRows;
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)s->sm_count * 2);
   k_dense_tc<<<grid, kTcThreads, kSmTotal, stream>>>(A);

@@ -373,22 +373,18 @@ sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
 
 sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream,
                               const HostPass *host) {
-  static bool attr_set[2][64] = {};
   if (p.flags & kPassHasTC) {
     if (s->dt != SV_C64 || p.m != kTcTileM || batch != 1 || p.nvec != 1)
       return set_error(SV_EINVAL, "internal: tensor-core tile pass needs one complex64 vector and 12-qubit tiles");
     return launch_tile_tc(s, p, stream);
   }
   const size_t smem = tile_smem(s->dt, p.m, (int)p.nvec);
-  const int dev = s->device & 63;
-  const int di = s->dt == SV_C64 ? 0 : 1;
-  if (!attr_set[di][dev]) {
-    if (s->dt == SV_C64) {
-      SV_CUDA(cudaFuncSetAttribute(k_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
-      SV_CUDA(cudaFuncSetAttribute(k_tile_inl, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
-    } else
-      SV_CUDA(cudaFuncSetAttribute(k_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
-    attr_set[di][dev] = true;
+  const cudaFuncAttribute kSmemAttr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (s->dt == SV_C64) {
+    SV_TRY(func_attr_once((const void *)k_tile<float>, s->device, kSmemAttr, 200 << 10));
+    SV_TRY(func_attr_once((const void *)k_tile_inl, s->device, kSmemAttr, 200 << 10));
+  } else {
+    SV_TRY(func_attr_once((const void *)k_tile<double>, s->device, kSmemAttr, 200 << 10));
   }
   if (smem > (200u << 10)) return set_error(SV_EINVAL, "tile too large for shared memory");
   dim3 grid((unsigned)(1ull << (p.n - p.m)), (unsigned)batch);
@@ -409,7 +405,7 @@ sv_status launch_tile_persist(sv_state *s, const PersistArgs &A, int m_max, int 
   const size_t smem = tile_smem(s->dt, m_max, 1);
   if (smem > (200u << 10)) return set_error(SV_EINVAL, "tile too large for shared memory");
   const void *fn = s->dt == SV_C64 ? (const void *)k_tile_persist<float> : (const void *)k_tile_persist<double>;
-  SV_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+  SV_TRY(func_attr_once(fn, s->device, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
   int per_sm = 0;
   SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTileMaxThreads, smem));
   if (per_sm < 1) return set_error(SV_EUNSUPPORTED, "persistent tile kernel does not fit on an SM");

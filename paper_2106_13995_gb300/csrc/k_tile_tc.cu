@@ -364,12 +364,8 @@ size_t tc_tile_smem(sv_prec mode) {
 sv_status launch_tile_tc(sv_state *s, const TilePass &p, cudaStream_t stream) {
   const sv_prec mode = (sv_prec)((p.flags >> 9) & 3);
   const size_t smem = tc_tile_smem(mode);
-  static bool attr = false;
-  if (!attr) {
-    SV_CUDA(cudaFuncSetAttribute(k_tile_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
-    SV_CUDA(cudaFuncSetAttribute(k_tile_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    attr = true;
-  }
+  SV_TRY(func_attr_once((const void *)k_tile_tc, s->device, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+  SV_TRY(func_attr_once((const void *)k_tile_tc, s->device, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   // CTAs per SM as shared memory and TMEM admit them (see tc_bufs); the
   // grid strides over the tiles, so CTAs that do not fit at once start later
   const uint64_t per_sm = mode == SV_PREC_TC_TF32X3 ? 2 : (uint64_t)kTcMinBlocks;

@@ -29,7 +29,8 @@ struct AdjointProgram {
   int n_inst = 0;
 };
 
-static std::map<std::pair<const sv_state *, uint64_t>, AdjointProgram> g_adj_cache;
+static ProgCache<AdjointProgram> g_adj_cache(64);
+void drop_adjoint_programs(const sv_state *s) { g_adj_cache.drop_owner(s); }
 
 static void append_passes(DeviceProgram &prog, std::vector<uint32_t> &op0s, const std::vector<PassPlan> &passes,
                           const BuildCtx &b, const std::vector<int> &bmo, sv_status &st) {
@@ -184,29 +185,23 @@ static sv_status adjoint_batch(sv_state *const *psi, sv_state *const *lam, int B
     if ((terms[t].x_mask & ~lim) || (terms[t].z_mask & ~lim))
       return set_error(SV_EINVAL, "Pauli mask references a qubit >= n");
   const Opts o1 = resolve(s, opt, 1), o2 = resolve(s, opt, 2);
-  // cache key: circuit structure, terms, options
-  uint64_t key = circuit_hash(c, 0xad);
-  {
-    uint64_t h = key;
-    auto mix = [&](const void *p, size_t n) {
-      const unsigned char *q = (const unsigned char *)p;
-      for (size_t i = 0; i < n; i++) h = (h ^ q[i]) * 1099511628211ull;
-    };
-    if (nt) mix(terms, sizeof(sv_pauli_term) * nt);
-    mix(&o1, sizeof(o1));
-    mix(&o2, sizeof(o2));
-    mix(&s->dt, sizeof(s->dt));
-    key = h;
+  // cache key: circuit structure, terms, options (parameters enter only the
+  // per-batch matrices, uploaded every call)
+  KeyBytes k;
+  k.val((int)0xad);
+  circuit_key(k, c);
+  if (nt) k.bytes(terms, sizeof(sv_pauli_term) * nt);
+  k.val(o1);
+  k.val(o2);
+  k.val(s->dt);
+  const uint64_t kh = k.hash();
+  std::shared_ptr<const AdjointProgram> Ap = g_adj_cache.find(s, k, kh);
+  if (!Ap) {
+    auto built = std::make_shared<AdjointProgram>();
+    SV_TRY(build_adjoint(s, c, params, terms, nt, o1, o2, *built));
+    Ap = g_adj_cache.insert(s, k, kh, std::move(built));
   }
-  auto ck = std::make_pair((const sv_state *)s, key);
-  auto it = g_adj_cache.find(ck);
-  if (it == g_adj_cache.end()) {
-    AdjointProgram A;
-    SV_TRY(build_adjoint(s, c, params, terms, nt, o1, o2, A));
-    if (g_adj_cache.size() > 16) g_adj_cache.clear();
-    it = g_adj_cache.emplace(ck, std::move(A)).first;
-  }
-  const AdjointProgram &A = it->second;
+  const AdjointProgram &A = *Ap;
   const int np = c->n_params;
   // per-batch matrices, state pointer tables
   std::vector<uint8_t> pm;

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <tuple>
 
 #include "sv_internal.h"
 
@@ -72,33 +73,51 @@ Opts resolve(const sv_state *s, const sv_options *o, int nvec) {
 }
 
 // ---------------------------------------------------------------------------
-// hashing (FNV-1a)
+// program cache keys
 // ---------------------------------------------------------------------------
-struct Hasher {
-  uint64_t h = 1469598103934665603ull;
-  void bytes(const void *p, size_t n) {
-    const unsigned char *c = (const unsigned char *)p;
-    for (size_t i = 0; i < n; i++) {
-      h ^= c[i];
-      h *= 1099511628211ull;
-    }
+uint64_t KeyBytes::hash() const {
+  // 8 bytes per step, each word mixed by a multiply-xorshift (splitmix64's
+  // finaliser); only a bucket index: equal hashes are compared byte for byte
+  uint64_t h = 0x243F6A8885A308D3ull ^ (uint64_t)b.size();
+  size_t i = 0;
+  for (; i + 8 <= b.size(); i += 8) {
+    uint64_t w;
+    std::memcpy(&w, b.data() + i, 8);
+    h = (h ^ w) * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 29;
   }
-  template <typename T> void val(const T &v) { bytes(&v, sizeof(T)); }
-};
+  uint64_t w = 0;
+  std::memcpy(&w, b.data() + i, b.size() - i);
+  h = (h ^ w) * 0xBF58476D1CE4E5B9ull;
+  return h ^ (h >> 31);
+}
 
-uint64_t circuit_hash(const sv_circuit *c, uint64_t salt) {
-  Hasher H;
-  H.val(salt);
-  H.val(c->n_qubits);
-  H.val(c->n_ops);
-  H.val(c->n_params);
-  if (c->n_ops > 0) H.bytes(c->ops, sizeof(sv_op) * (size_t)c->n_ops);
+void circuit_key(KeyBytes &k, const sv_circuit *c) {
+  k.val(c->n_qubits);
+  k.val(c->n_ops);
+  k.val(c->n_params);
+  if (c->n_ops > 0) k.bytes(c->ops, sizeof(sv_op) * (size_t)c->n_ops);
   for (int i = 0; i < c->n_ops; i++)
     if (c->ops[i].gate == SV_GATE_MATRIX && c->matrices && c->ops[i].matrix_offset >= 0) {
       const int d = 1 << c->ops[i].n_targets;
-      H.bytes(c->matrices + 2 * c->ops[i].matrix_offset, sizeof(double) * 2 * d * d);
+      k.bytes(c->matrices + 2 * c->ops[i].matrix_offset, sizeof(double) * 2 * d * d);
     }
-  return H.h;
+}
+
+static std::atomic<uint64_t> g_serial{0};
+uint64_t next_program_serial() { return ++g_serial; }
+
+// kernel attributes, once per (kernel, device, attribute, value)
+static std::mutex g_attr_mu;
+static std::vector<std::tuple<const void *, int, int, int>> g_attr_done;
+sv_status func_attr_once(const void *fn, int device, cudaFuncAttribute attr, int value) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  const auto key = std::make_tuple(fn, device, (int)attr, value);
+  for (const auto &t : g_attr_done)
+    if (t == key) return SV_OK;
+  SV_CUDA(cudaFuncSetAttribute(fn, attr, value));
+  g_attr_done.push_back(key);
+  return SV_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -293,7 +312,7 @@ sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, si
                        const std::vector<size_t> &offs, size_t total) {
   if (total > kWsProgBytes) return set_error(SV_ENOMEM, "gate program exceeds the workspace program area");
   SV_TRY(stage_upload_to(s, s->ws + kWsProg, parts, offs, total));
-  s->resident_key = 0;
+  s->resident = 0;
   return SV_OK;
 }
 
@@ -329,7 +348,7 @@ sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &
   return SV_OK;
 }
 
-static std::map<std::pair<const sv_state *, uint64_t>, CachedProgram> g_cache;
+static ProgCache<CachedProgram> g_cache(kProgramCacheDefault);
 
 static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gates, const Opts &o,
                                        CachedProgram &out) {
@@ -433,8 +452,8 @@ static sv_status run_blocks_per_gate(sv_state *s, const std::vector<Block> &bloc
   return SV_OK;
 }
 
-sv_status upload_program(sv_state *s, const CachedProgram &cp, uint64_t key) {
-  if (s->resident_key == key && key != 0) return SV_OK;
+sv_status upload_program(sv_state *s, const CachedProgram &cp) {
+  if (s->resident == cp.serial && cp.serial != 0) return SV_OK;
   const DeviceProgram &p = cp.prog;
   std::vector<std::pair<const void *, size_t>> parts = {
       {p.ops.data(), p.ops.size() * sizeof(TileOp)},
@@ -442,39 +461,38 @@ sv_status upload_program(sv_state *s, const CachedProgram &cp, uint64_t key) {
       {p.coeffs.data(), p.coeffs.size() * sizeof(double)}};
   std::vector<size_t> offs = {cp.lay.ops_off, cp.lay.mats_off, cp.lay.coeffs_off};
   SV_TRY(stage_upload(s, parts, offs, cp.lay.end));
-  s->resident_key = key;
+  s->resident = cp.serial;
   return SV_OK;
 }
 
 sv_status get_program(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
-                      const CachedProgram **out, uint64_t *key_out, Opts *o_out) {
+                      ProgramRef *out, Opts *o_out) {
   if (!s) return set_error(SV_EINVAL, "null state");
   if (!c) return set_error(SV_EINVAL, "null circuit");
   Opts o = resolve(s, opt, 1);
   tuned_options(s, c, opt, o);
-  Hasher H;
-  H.val(circuit_hash(c, 0x51));
-  H.val(o.fusion_k);
-  H.val(o.tile_m);
-  H.val(o.L);
-  H.val(o.mode);
-  H.val(o.prec);
-  H.val(o.tc_in_tile);
-  H.val((int)s->dt);
-  if (params && c->n_params > 0) H.bytes(params, sizeof(double) * c->n_params);
-  const uint64_t key = H.h;
-  auto ck = std::make_pair((const sv_state *)s, key);
-  auto it = g_cache.find(ck);
-  if (it == g_cache.end()) {
+  KeyBytes k;
+  k.val((int)0x51);
+  circuit_key(k, c);
+  k.val(o.fusion_k);
+  k.val(o.tile_m);
+  k.val(o.L);
+  k.val(o.mode);
+  k.val(o.prec);
+  k.val(o.tc_in_tile);
+  k.val((int)s->dt);
+  if (params && c->n_params > 0) k.bytes(params, sizeof(double) * c->n_params);
+  const uint64_t h = k.hash();
+  ProgramRef cp = g_cache.find(s, k, h);
+  if (!cp) {
     std::vector<Gate> gates;
     SV_TRY(circuit_to_gates(c, params, s->n, gates, false));
-    CachedProgram cp;
-    SV_TRY(build_circuit_program(s, gates, o, cp));
-    if (g_cache.size() > 2048) g_cache.clear();
-    it = g_cache.emplace(ck, std::move(cp)).first;
+    auto built = std::make_shared<CachedProgram>();
+    SV_TRY(build_circuit_program(s, gates, o, *built));
+    built->serial = next_program_serial();
+    cp = g_cache.insert(s, k, h, std::move(built));
   }
-  *out = &it->second;
-  *key_out = key;
+  *out = std::move(cp);
   *o_out = o;
   return SV_OK;
 }
@@ -506,6 +524,10 @@ const char *sv_status_string(sv_status st) {
 }
 
 uint64_t sv_kernel_launch_count(void) { return g_launches.load(); }
+
+int64_t sv_program_cache_limit(int64_t max_programs) {
+  return (int64_t)g_cache.set_limit(max_programs > 0 ? (size_t)max_programs : 0);
+}
 
 size_t sv_workspace_bytes(int n, sv_dtype dt) {
   (void)dt;
@@ -560,8 +582,8 @@ sv_status sv_create(int n, sv_dtype dt, void *amps, size_t amps_bytes, void *ws,
 sv_status sv_destroy(sv_state *s) {
   if (!s) return SV_OK;
   cudaStreamSynchronize(s->stream);
-  for (auto it = g_cache.begin(); it != g_cache.end();)
-    it = (it->first.first == s) ? g_cache.erase(it) : std::next(it);
+  g_cache.drop_owner(s);
+  drop_adjoint_programs(s);
   drop_graphs(s);
   if (s->capture) cudaStreamDestroy(s->capture);
   if (s->staged) cudaEventDestroy(s->staged);
@@ -644,12 +666,11 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
 
 
 sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt) {
-  const CachedProgram *cp = nullptr;
-  uint64_t key = 0;
+  ProgramRef cp;
   Opts o;
-  SV_TRY(get_program(s, c, params, opt, &cp, &key, &o));
+  SV_TRY(get_program(s, c, params, opt, &cp, &o));
   if (o.mode == SV_MODE_PER_GATE) return run_blocks_per_gate(s, cp->blocks);
-  SV_TRY(upload_program(s, *cp, key));
+  SV_TRY(upload_program(s, *cp));
   LaunchEnv E;
   E.v0 = s->amps;
   return launch_program(s, cp->prog, cp->lay, cp->op0s, E);
@@ -657,10 +678,9 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *param
 
 sv_status sv_plan_info(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
                        int64_t *n_blocks, int64_t *n_passes) {
-  const CachedProgram *cp = nullptr;
-  uint64_t key = 0;
+  ProgramRef cp;
   Opts o;
-  SV_TRY(get_program(s, c, params, opt, &cp, &key, &o));
+  SV_TRY(get_program(s, c, params, opt, &cp, &o));
   if (n_blocks) *n_blocks = (int64_t)cp->blocks.size();
   if (n_passes) *n_passes = o.mode == SV_MODE_PER_GATE ? (int64_t)cp->blocks.size() : (int64_t)cp->prog.passes.size();
   return SV_OK;
@@ -669,10 +689,9 @@ sv_status sv_plan_info(sv_state *s, const sv_circuit *c, const double *params, c
 sv_status sv_plan_fmas(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
                        double *fma_per_amp) {
   if (!fma_per_amp) return set_error(SV_EINVAL, "null argument");
-  const CachedProgram *cp = nullptr;
-  uint64_t key = 0;
+  ProgramRef cp;
   Opts o;
-  SV_TRY(get_program(s, c, params, opt, &cp, &key, &o));
+  SV_TRY(get_program(s, c, params, opt, &cp, &o));
   double f = 0;
   for (const Block &b : cp->blocks) {
     if (b.kind != TOP_DENSE) continue;

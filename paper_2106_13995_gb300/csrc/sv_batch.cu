@@ -86,24 +86,30 @@ struct BatchGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
-static std::map<std::pair<const sv_state *, uint64_t>, BatchGraph> g_graphs;
+// key: the first state and, per state, (program serial, amplitudes,
+// workspace, wide flag), plus the wait budget -- everything the recorded
+// launches depend on
+using GraphKey = std::pair<const sv_state *, std::vector<uint64_t>>;
+static std::map<GraphKey, BatchGraph> g_graphs;
+static std::mutex g_graphs_mu;
+constexpr size_t kMaxGraphs = 64;
 
 constexpr uint64_t kDefaultSpin = 1ull << 23;   // ~1 s of 128 ns polls
 
 static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *const *circs,
                            const double *const *params, const sv_options *opt) {
   sv_state *s0 = states[0];
-  std::vector<const CachedProgram *> cps(B);
-  std::vector<uint64_t> keys(B);
+  // the programs stay alive for the whole call even if the cache evicts them
+  std::vector<ProgramRef> cps(B);
   std::vector<Opts> os(B);
   int maxP = 0, m_max = 1;
   for (int b = 0; b < B; b++) {
-    SV_TRY(get_program(states[b], circs[b], params ? params[b] : nullptr, opt, &cps[b], &keys[b], &os[b]));
+    SV_TRY(get_program(states[b], circs[b], params ? params[b] : nullptr, opt, &cps[b], &os[b]));
     if (os[b].mode == SV_MODE_PER_GATE) return set_error(SV_EINVAL, "per-gate mode has no batched form");
     maxP = std::max(maxP, (int)cps[b]->prog.passes.size());
     for (const TilePass &tp : cps[b]->prog.passes) m_max = std::max(m_max, tp.m);
   }
-  for (int b = 0; b < B; b++) SV_TRY(upload_program(states[b], *cps[b], keys[b]));
+  for (int b = 0; b < B; b++) SV_TRY(upload_program(states[b], *cps[b]));
   // States whose passes have at least 2 tiles per SM fill the GPU with one
   // ordinary launch per pass; the persistent queue is for the rest, whose
   // passes alone would leave most SMs idle.
@@ -122,7 +128,6 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
   std::vector<uint32_t> ntiles, chunk;
   std::vector<int> last_desc(B, -1);
   unsigned long long items = 0;
-  uint64_t hkey = 1469598103934665603ull;
   for (int p = 0; p < maxP; p++)
     for (int b = 0; b < B; b++) {
       const CachedProgram &cp = *cps[b];
@@ -144,7 +149,6 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
       chunk.push_back(ch);
       last_desc[b] = (int)desc.size() - 1;
       items += (nt + ch - 1) / ch;
-      hkey = (hkey ^ keys[b] ^ (uint64_t)(uintptr_t)states[b]->amps ^ (uint64_t)p) * 1099511628211ull;
     }
   const uint32_t nd = (uint32_t)desc.size();
   // the wide states' passes, as ordinary launches on stream st
@@ -164,12 +168,9 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
         const HostPass hp{cp.prog.ops.data() + cp.op0s[p], cp.prog.mats.data()};
         SV_TRY(launch_any_pass(states[b], tp, 1, st, &hp));
       }
-      hkey = (hkey ^ keys[b] ^ (uint64_t)(uintptr_t)states[b]->amps) * 1099511628211ull;
     }
     return SV_OK;
   };
-  for (int b = 0; b < B; b++)
-    if (wide[b]) hkey = (hkey ^ keys[b] ^ (uint64_t)(uintptr_t)states[b]->amps ^ 0x77) * 1099511628211ull;
   const bool use_graph = opt && opt->mode == SV_MODE_TILED_GRAPH;
   if (nd == 0) {
     if (!use_graph) return launch_wide(s0->stream);
@@ -217,7 +218,17 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
   if (!use_graph) return record(s0->stream);
   // graph: capture the counter reset and the cooperative launch once per
   // batch layout, then replay
-  auto gk = std::make_pair((const sv_state *)s0, hkey ^ A.spin_limit);
+  GraphKey gk;
+  gk.first = s0;
+  gk.second.reserve(4 * (size_t)B + 1);
+  for (int b = 0; b < B; b++) {
+    gk.second.push_back(cps[b]->serial);
+    gk.second.push_back((uint64_t)(uintptr_t)states[b]->amps);
+    gk.second.push_back((uint64_t)(uintptr_t)states[b]->ws);
+    gk.second.push_back((uint64_t)wide[b]);
+  }
+  gk.second.push_back(A.spin_limit);
+  std::lock_guard<std::mutex> lk(g_graphs_mu);
   auto it = g_graphs.find(gk);
   if (it == g_graphs.end()) {
     BatchGraph g;
@@ -233,14 +244,17 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
     }
     if (e2 != cudaSuccess) return cuda_error(e2, "cudaStreamEndCapture");
     SV_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
-    if (g_graphs.size() > 64) {
+    if (g_graphs.size() >= kMaxGraphs) {
+      // earlier replays may still be running on this stream: let them finish
+      // before their executable graphs go
+      SV_CUDA(cudaStreamSynchronize(s0->stream));
       for (auto &kv : g_graphs) {
         cudaGraphExecDestroy(kv.second.exec);
         cudaGraphDestroy(kv.second.graph);
       }
       g_graphs.clear();
     }
-    it = g_graphs.emplace(gk, g).first;
+    it = g_graphs.emplace(std::move(gk), g).first;
   }
   SV_CUDA(cudaGraphLaunch(it->second.exec, s0->stream));
   g_launches++;
@@ -248,6 +262,7 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
 }
 
 void drop_graphs(const sv_state *s) {
+  std::lock_guard<std::mutex> lk(g_graphs_mu);
   for (auto it = g_graphs.begin(); it != g_graphs.end();) {
     if (it->first.first == s) {
       cudaGraphExecDestroy(it->second.exec);

@@ -8,6 +8,10 @@
 
 #include <atomic>
 #include <complex>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -232,9 +236,7 @@ struct sv_state {
   size_t pinned_bytes = 0;
   cudaEvent_t staged = nullptr;     // last upload from `pinned` finished
   cudaStream_t capture = nullptr;   // library-owned stream used only to record CUDA graphs
-  // program cache: key -> program
-  std::unordered_map<uint64_t, sv::DeviceProgram> programs;
-  uint64_t resident_key = 0;        // program currently in the workspace program area
+  uint64_t resident = 0;            // serial of the program in the workspace program area (0: none)
 };
 
 namespace sv {
@@ -287,26 +289,116 @@ struct LaunchEnv {
 };
 sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &L,
                          const std::vector<uint32_t> &op0s, const LaunchEnv &E);
-struct Opts {
+struct Opts {   // all int: hashed as key bytes, so no padding
   int fusion_k, tile_m, L, prec, mode;
-  bool tc_in_tile = false;
+  int tc_in_tile = 0;
 };
 Opts resolve(const sv_state *s, const sv_options *o, int nvec);
 // Fill fusion_k / tile_m that the caller left at 0 from the autotuner's
 // cache for this circuit's shape (sv_batch.cu).
 void tuned_options(const sv_state *s, const sv_circuit *c, const sv_options *opt, Opts &o);
+// ---------------------------------------------------------------------------
+// program caches
+// ---------------------------------------------------------------------------
+// Key material of a cached program: every byte that determines it (circuit
+// ops and matrices, parameters, resolved options, dtype).  Lookups hash it
+// and compare it byte for byte on a hash hit, so a collision never returns
+// another circuit's program.
+struct KeyBytes {
+  std::vector<uint8_t> b;
+  void bytes(const void *p, size_t n) {
+    const uint8_t *q = static_cast<const uint8_t *>(p);
+    b.insert(b.end(), q, q + n);
+  }
+  template <typename T> void val(const T &v) { bytes(&v, sizeof(T)); }
+  uint64_t hash() const;
+};
+// key material of a circuit (ops, the matrices its MATRIX ops use)
+void circuit_key(KeyBytes &k, const sv_circuit *c);
+uint64_t next_program_serial();
+
+// A bounded, thread-safe cache of immutable programs per state handle.
+// Entries are shared: a caller holding one keeps it alive even after the
+// cache evicts it (oldest first once more than `limit` are held).
+template <class V> class ProgCache {
+ public:
+  explicit ProgCache(size_t limit) : limit_(limit) {}
+  std::shared_ptr<const V> find(const void *owner, const KeyBytes &k, uint64_t h) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto r = map_.equal_range(h);
+    for (auto it = r.first; it != r.second; ++it)
+      if (it->second.owner == owner && it->second.key == k.b) return it->second.val;
+    return nullptr;
+  }
+  // Insert v unless an equal key is present; returns the cached entry.
+  std::shared_ptr<const V> insert(const void *owner, const KeyBytes &k, uint64_t h, std::shared_ptr<const V> v) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto r = map_.equal_range(h);
+    for (auto it = r.first; it != r.second; ++it)
+      if (it->second.owner == owner && it->second.key == k.b) return it->second.val;
+    const uint64_t seq = ++seq_;
+    map_.emplace(h, Entry{owner, k.b, v, seq});
+    order_.emplace_back(h, seq);
+    while (map_.size() > limit_ && !order_.empty()) {
+      erase_locked(order_.front().first, order_.front().second);
+      order_.pop_front();
+    }
+    return v;
+  }
+  void drop_owner(const void *owner) {
+    std::lock_guard<std::mutex> lk(mu_);
+    for (auto it = map_.begin(); it != map_.end();) it = it->second.owner == owner ? map_.erase(it) : std::next(it);
+  }
+  size_t set_limit(size_t n) {
+    std::lock_guard<std::mutex> lk(mu_);
+    const size_t old = limit_;
+    if (n > 0) limit_ = n;
+    return old;
+  }
+  size_t size() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return map_.size();
+  }
+
+ private:
+  struct Entry {
+    const void *owner;
+    std::vector<uint8_t> key;
+    std::shared_ptr<const V> val;
+    uint64_t seq;
+  };
+  void erase_locked(uint64_t h, uint64_t seq) {
+    auto r = map_.equal_range(h);
+    for (auto it = r.first; it != r.second; ++it)
+      if (it->second.seq == seq) {
+        map_.erase(it);
+        return;
+      }
+  }
+  std::mutex mu_;
+  std::unordered_multimap<uint64_t, Entry> map_;
+  std::deque<std::pair<uint64_t, uint64_t>> order_;
+  uint64_t seq_ = 0;
+  size_t limit_;
+};
+
 // Cached plain-circuit program (one vector) and its lookup.
 struct CachedProgram {
   DeviceProgram prog;
   std::vector<uint32_t> op0s;
   ProgLayout lay;
   std::vector<Block> blocks;   // for per-gate mode
+  uint64_t serial = 0;         // unique per built program (workspace residency tag)
 };
+using ProgramRef = std::shared_ptr<const CachedProgram>;
+constexpr size_t kProgramCacheDefault = 2048;
 sv_status get_program(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt,
-                      const CachedProgram **out, uint64_t *key_out, Opts *o_out);
-sv_status upload_program(sv_state *s, const CachedProgram &cp, uint64_t key);
+                      ProgramRef *out, Opts *o_out);
+sv_status upload_program(sv_state *s, const CachedProgram &cp);
+// Set a kernel attribute once per (kernel, device, attribute, value); thread-safe.
+sv_status func_attr_once(const void *fn, int device, cudaFuncAttribute attr, int value);
 void drop_graphs(const sv_state *s);
-uint64_t circuit_hash(const sv_circuit *c, uint64_t salt);
+void drop_adjoint_programs(const sv_state *s);
 
 // kernels (launchers), all enqueue on s->stream
 sv_status launch_set_basis(sv_state *s, uint64_t index);

@@ -78,6 +78,18 @@ sv_status sv_expect_z_all_noalloc(const void *amps_dev, int n_qubits, sv_dtype d
   if (dtype != SV_C64 && dtype != SV_C128) return set_error(SV_EINVAL, "unknown dtype");
   if ((uintptr_t)amps_dev & 255) return set_error(SV_EINVAL, "amplitudes must be 256-byte aligned");
   if ((uintptr_t)out_dev & 7) return set_error(SV_EINVAL, "output must be 8-byte aligned");
+  // both buffers must be memory the current device can address: a host
+  // pointer or another device's memory would make the kernels fault
+  int cur = 0;
+  SV_CUDA(cudaGetDevice(&cur));
+  for (const void *p : {amps_dev, static_cast<const void *>(out_dev)}) {
+    cudaPointerAttributes attr;
+    SV_CUDA(cudaPointerGetAttributes(&attr, p));
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+      return set_error(SV_EINVAL, "amplitudes and output must be device memory");
+    if (attr.type == cudaMemoryTypeDevice && attr.device != cur)
+      return set_error(SV_EINVAL, "amplitudes and output must be on the current device");
+  }
   return zall_noalloc(amps_dev, n_qubits, dtype, out_dev, (cudaStream_t)stream);
 }
 

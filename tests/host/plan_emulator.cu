@@ -9,6 +9,7 @@
 // a GPU.
 #include <complex>
 #include <cstdio>
+#include <cstring>
 #include <set>
 #include <vector>
 
@@ -253,4 +254,50 @@ extern "C" int check_op_pre(const sv_circuit *c, int m, int L) {
     }
   }
   return checked;
+}
+
+// The library's program cache, driven past its bound on a host-only state
+// handle (planning touches no device): with the bound at `limit`, the first
+// circuit's program is held while `nc` circuits are planned in turn (as one
+// batched call does); the held program must stay intact after its entry is
+// evicted, every lookup must return the program of its own circuit (same
+// blocks as a fresh plan), a repeated lookup must hit the cache, and the
+// cache must stay within its bound.  Returns 0, or the number of the failed
+// check.
+static bool same_program(const CachedProgram &a, const CachedProgram &b) {
+  if (a.prog.ops.size() != b.prog.ops.size() || a.prog.mats != b.prog.mats) return false;
+  if (std::memcmp(a.prog.ops.data(), b.prog.ops.data(), a.prog.ops.size() * sizeof(TileOp)) != 0) return false;
+  return a.blocks.size() == b.blocks.size();
+}
+extern "C" int cache_selftest(const sv_circuit *const *cs, int nc, int limit) {
+  sv_state st;
+  st.n = cs[0]->n_qubits;
+  st.dt = SV_C64;
+  const int64_t old = sv_program_cache_limit(limit);
+  int rc = 0;
+  {
+    ProgramRef held;
+    Opts o;
+    if (get_program(&st, cs[0], nullptr, nullptr, &held, &o) != SV_OK) rc = 1;
+    const CachedProgram snapshot = rc ? CachedProgram() : *held;
+    ProgramRef again;
+    if (!rc && (get_program(&st, cs[0], nullptr, nullptr, &again, &o) != SV_OK || again != held)) rc = 2;
+    for (int i = 1; i < nc && !rc; i++) {
+      ProgramRef p;
+      if (get_program(&st, cs[i], nullptr, nullptr, &p, &o) != SV_OK) { rc = 3; break; }
+      // a fresh plan of the same circuit, outside the cache
+      std::vector<Gate> gates;
+      circuit_to_gates(cs[i], nullptr, st.n, gates, false);
+      const std::vector<Block> blocks = fuse(gates, o.fusion_k);
+      if (p->blocks.size() != blocks.size()) rc = 4;
+      if (p->serial == held->serial) rc = 5;
+    }
+    if (!rc && !same_program(snapshot, *held)) rc = 6;   // evicted but still held, intact
+    ProgramRef back;
+    if (!rc && get_program(&st, cs[0], nullptr, nullptr, &back, &o) != SV_OK) rc = 7;
+    if (!rc && nc > limit && back->serial == held->serial) rc = 8;   // it was evicted: rebuilt
+    if (!rc && !same_program(*back, *held)) rc = 9;
+  }
+  sv_program_cache_limit(old);
+  return rc;
 }

@@ -162,3 +162,25 @@ def test_uneven_circuits_tensor_core_modes(svlib, oracle, prec):
         s = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c, opts=svlib.options(prec=prec))
         inf, _ = fidelity_metrics(oracle.run(c), s.numpy())
         assert inf <= 1e-5, (c.name, prec, inf)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_beyond_program_cache_bound(svlib, graph):
+    """A batch of more distinct circuits than the program cache holds: the
+    cache evicts entries while the call still uses them, and the results
+    stay bit-identical to one call per circuit."""
+    from paper_2106_13995_gb300 import _native as N
+    circs = [W.random_u3_cz(10, 3, seed) for seed in range(40)]
+    old = N.lib().sv_program_cache_limit(8)
+    try:
+        states = [svlib.StateVector(10, "c64").set_basis(0) for _ in circs]
+        opts = svlib.options(mode=N.SV_MODE_TILED_GRAPH) if graph else None
+        for rep in range(2 if graph else 1):
+            for s in states:
+                s.set_basis(0)
+            batch_apply(svlib, states, circs, opts)
+        for c, s in zip(circs, states):
+            ref = svlib.StateVector(10, "c64").set_basis(0).apply_circuit(c).numpy()
+            assert np.array_equal(s.numpy(), ref), c.name
+    finally:
+        N.lib().sv_program_cache_limit(old)

@@ -128,3 +128,18 @@ def test_op_setup_records_match_direct_slots(emu):
                  (W.random_gate_circuit(11, 60, seed=2), 9), (W.multiplier(3), 10)):
         mm = sim.marshal(c)
         assert emu.check_op_pre(C.addressof(mm.c), min(m, c.n_qubits), 3) > 0, c.name
+
+
+def test_program_cache_eviction_keeps_held_programs(emu):
+    """The program cache with a small bound, driven past it while an early
+    entry is held (the pattern of one batched call over many circuits): the
+    held program stays intact, each lookup returns its own circuit's
+    program, and an evicted circuit is rebuilt to the same program."""
+    from paper_2106_13995_gb300 import sim
+    circs = [W.random_u3_cz(10, 2, seed) for seed in range(40)]
+    ms = [sim.marshal(c) for c in circs]
+    arr = (C.c_void_p * len(ms))(*[C.addressof(m.c) for m in ms])
+    emu.cache_selftest.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    assert emu.cache_selftest(arr, len(ms), 8) == 0
+    # a bound larger than the number of circuits: nothing is evicted
+    assert emu.cache_selftest(arr, 5, 64) == 0
