@@ -123,7 +123,7 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
         if ((base & gcm) != gcm) break;
         if constexpr (INL && sizeof(R) == 4) {
           if (op.gen & kGenInline) {   // single vector: vmask is 1
-            apply_op_inl(reinterpret_cast<float2 *>(v0), P.m, op, *I, oi);
+            apply_op_inl(reinterpret_cast<float2 *>(v0), P.m, op, *I, oi, threadIdx.x, blockDim.x);
             break;
           }
           if (op.kind == TOP_DENSE && op.k <= 3) {
@@ -135,8 +135,8 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
           }
         }
         const C *U = ((op.gen & kGenBatchMat) ? pmats : mats) + op.mat;
-        if (op.vmask & 1) apply_op<R, INL>(v0, P.m, op, P.ops + oi, U);
-        if (op.vmask & 2) apply_op<R, INL>(v1, P.m, op, P.ops + oi, U);
+        if (op.vmask & 1) apply_op<R, INL>(v0, P.m, op, P.ops + oi, U, threadIdx.x, blockDim.x);
+        if (op.vmask & 2) apply_op<R, INL>(v1, P.m, op, P.ops + oi, U, threadIdx.x, blockDim.x);
         break;
       }
       case TOP_GRAD:

@@ -114,7 +114,8 @@ __device__ __forceinline__ void ld_pair(const double2 *p, double2 &a, double2 &b
 // serving G groups.
 template <typename R, int K, int G>
 __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
-                                         const typename Cx<R>::T *__restrict__ U) {
+                                         const typename Cx<R>::T *__restrict__ U,
+                                         uint32_t tid, uint32_t T) {
   using C = typename Cx<R>::T;
   constexpr int D = 1 << K;
   constexpr bool kRegU = K <= 2;
@@ -137,12 +138,11 @@ __device__ __forceinline__ void dense_op(typename Cx<R>::T *__restrict__ v, int 
   }
   const uint32_t fixed = tmask | op.lcmask;
   const uint32_t ngroups = 1u << (m - __popc(fixed));
-  const uint32_t T = blockDim.x;
-  if (threadIdx.x >= ngroups) return;
+  if (tid >= ngroups) return;
   // thread t's groups are t + c T, c < ntrips; slot(t + c T) = slot(t) ^
   // slot(c T), and a trip's G groups c0 + h share slot(c0 T)
   const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
-  const uint32_t sthr = swb<R>(thread_l(threadIdx.x, op) | op.lcmask);
+  const uint32_t sthr = swb<R>(thread_l(tid, op) | op.lcmask);
   const TripMap tm = trip_map(T, fixed);
   uint32_t dh[G];
 #pragma unroll
@@ -256,7 +256,8 @@ struct GlobalPairs {
   }
 };
 template <int K, int G, class Src>
-__device__ __forceinline__ void dense_pairs(float2 *__restrict__ v, int m, const TileOp &op, const Src &src) {
+__device__ __forceinline__ void dense_pairs(float2 *__restrict__ v, int m, const TileOp &op, const Src &src,
+                                            uint32_t tid, uint32_t T) {
   constexpr int D = 1 << K, NP = D / 2;
   const uint32_t vs = smem_u32(v);
   uint32_t soff[D], tmask = 0;
@@ -276,12 +277,11 @@ __device__ __forceinline__ void dense_pairs(float2 *__restrict__ v, int m, const
   }
   const uint32_t fixed = tmask | op.lcmask;
   const uint32_t ngroups = 1u << (m - __popc(fixed));
-  const uint32_t T = blockDim.x;
-  if (threadIdx.x >= ngroups) return;
+  if (tid >= ngroups) return;
   // thread t's groups are t + c T, c < ntrips; slot(t + c T) = slot(t) ^
   // slot(c T), and a trip's G groups c0 + h share slot(c0 T)
   const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
-  const uint32_t sthr = swb<float>(thread_l(threadIdx.x, op) | op.lcmask);
+  const uint32_t sthr = swb<float>(thread_l(tid, op) | op.lcmask);
   TripMap tm;
   uint32_t dh[G];
   if constexpr (Src::kPre) {
@@ -358,23 +358,25 @@ template <int K> constexpr int kPairsGlobalG = K == 1 ? 4 : (K == 2 ? 2 : 1);
 // WIDE: the kernel has registers to spare (128 a thread): two groups per
 // trip for 3-qubit blocks
 template <bool WIDE = false>
-__device__ __forceinline__ void dense_pairs_global(float2 *v, int m, const TileOp &op, const float2 *U) {
+__device__ __forceinline__ void dense_pairs_global(float2 *v, int m, const TileOp &op, const float2 *U,
+                                                   uint32_t tid, uint32_t T) {
   const GlobalPairs src{U};
   switch (op.k) {
-    case 1: dense_pairs<1, kPairsGlobalG<1>>(v, m, op, src); break;
-    case 2: dense_pairs<2, kPairsGlobalG<2>>(v, m, op, src); break;
-    default: dense_pairs<3, WIDE ? 2 : kPairsGlobalG<3>>(v, m, op, src); break;
+    case 1: dense_pairs<1, kPairsGlobalG<1>>(v, m, op, src, tid, T); break;
+    case 2: dense_pairs<2, kPairsGlobalG<2>>(v, m, op, src, tid, T); break;
+    default: dense_pairs<3, WIDE ? 2 : kPairsGlobalG<3>>(v, m, op, src, tid, T); break;
   }
 }
 
 // Dense complex64 block of 1-3 qubits whose matrix is in the launch's
 // parameter block (op.mat indexes TileInline::mats, stored as row pairs).
-__device__ __forceinline__ void apply_op_inl(float2 *v, int m, const TileOp &op, const TileInline &I, int oi) {
+__device__ __forceinline__ void apply_op_inl(float2 *v, int m, const TileOp &op, const TileInline &I, int oi,
+                                             uint32_t tid, uint32_t T) {
   const ParamPairs src{I, op.mat, (uint32_t)oi};
   switch (op.k) {
-    case 1: dense_pairs<1, kPairsG<1>>(v, m, op, src); break;
-    case 2: dense_pairs<2, kPairsG<2>>(v, m, op, src); break;
-    default: dense_pairs<3, kPairsG<3>>(v, m, op, src); break;
+    case 1: dense_pairs<1, kPairsG<1>>(v, m, op, src, tid, T); break;
+    case 2: dense_pairs<2, kPairsG<2>>(v, m, op, src, tid, T); break;
+    default: dense_pairs<3, kPairsG<3>>(v, m, op, src, tid, T); break;
   }
 }
 
@@ -384,9 +386,10 @@ __device__ __forceinline__ void apply_op_inl(float2 *v, int m, const TileOp &op,
 // caller keeps an addressable (local-memory) copy of it.
 template <typename R, int K>
 __device__ __noinline__ void dense_op_big(typename Cx<R>::T *__restrict__ v, int m, const TileOp *gop,
-                                          const typename Cx<R>::T *__restrict__ U) {
+                                          const typename Cx<R>::T *__restrict__ U, uint32_t tid,
+                                          uint32_t T) {
   const TileOp op = *gop;
-  dense_op<R, K, 1>(v, m, op, U);
+  dense_op<R, K, 1>(v, m, op, U, tid, T);
 }
 
 // Diagonal block: amplitude l is multiplied by d[r(l)], r(l) the target bits
@@ -394,12 +397,12 @@ __device__ __noinline__ void dense_op_big(typename Cx<R>::T *__restrict__ v, int
 // part and a warp-uniform trip part.
 template <typename R>
 __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m, const TileOp &op,
-                                        const typename Cx<R>::T *__restrict__ d) {
+                                        const typename Cx<R>::T *__restrict__ d, uint32_t tid,
+                                        uint32_t T) {
   using C = typename Cx<R>::T;
   unsigned char *vb = reinterpret_cast<unsigned char *>(v);
   const uint32_t ngroups = 1u << (m - __popc(op.lcmask));
-  const uint32_t T = blockDim.x;
-  if (threadIdx.x >= ngroups) return;
+  if (tid >= ngroups) return;
   uint32_t tpos[6];
 #pragma unroll
   for (int j = 0; j < 6; j++) tpos[j] = op.t[j];
@@ -411,7 +414,7 @@ __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m
       if (j < k) r |= ((l >> tpos[j]) & 1u) << j;
     return r;
   };
-  const uint32_t lthr = thread_l(threadIdx.x, op) | op.lcmask;
+  const uint32_t lthr = thread_l(tid, op) | op.lcmask;
   const uint32_t sthr = swb<R>(lthr), rthr = rows(lthr);
   const TripMap tm = trip_map(T, op.lcmask);
   for (uint32_t g0 = 0, c = 0; g0 < ngroups; g0 += T, c++) {
@@ -426,15 +429,15 @@ __device__ __forceinline__ void diag_op(typename Cx<R>::T *__restrict__ v, int m
 // registers off the hot path)
 template <typename R, bool kSmallInParams = false, bool kWideRegs = false>
 __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const TileOp &op, const TileOp *gop,
-                                         const typename Cx<R>::T *U) {
+                                         const typename Cx<R>::T *U, uint32_t tid, uint32_t T) {
   if (op.kind == TOP_DIAG) {
-    diag_op<R>(v, m, op, U);
+    diag_op<R>(v, m, op, U, tid, T);
     return;
   }
   if constexpr (sizeof(R) == 4) {
     if constexpr (!kSmallInParams) {
       if (op.k <= 3) {
-        dense_pairs_global<kWideRegs>(v, m, op, U);
+        dense_pairs_global<kWideRegs>(v, m, op, U, tid, T);
         return;
       }
     }
@@ -442,12 +445,12 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
   switch (op.k) {
     // groups per trip: as many as the registers allow next to a thread's
     // amplitudes (complex128 needs twice the registers per amplitude)
-    case 1: dense_op<R, 1, sizeof(R) == 4 ? 4 : 2>(v, m, op, U); break;
-    case 2: dense_op<R, 2, sizeof(R) == 4 ? 2 : 1>(v, m, op, U); break;
-    case 3: dense_op<R, 3, sizeof(R) == 4 ? 2 : 1>(v, m, op, U); break;
-    case 4: dense_op_big<R, 4>(v, m, gop, U); break;
-    case 5: dense_op_big<R, 5>(v, m, gop, U); break;
-    default: dense_op_big<R, 6>(v, m, gop, U); break;
+    case 1: dense_op<R, 1, sizeof(R) == 4 ? 4 : 2>(v, m, op, U, tid, T); break;
+    case 2: dense_op<R, 2, sizeof(R) == 4 ? 2 : 1>(v, m, op, U, tid, T); break;
+    case 3: dense_op<R, 3, sizeof(R) == 4 ? 2 : 1>(v, m, op, U, tid, T); break;
+    case 4: dense_op_big<R, 4>(v, m, gop, U, tid, T); break;
+    case 5: dense_op_big<R, 5>(v, m, gop, U, tid, T); break;
+    default: dense_op_big<R, 6>(v, m, gop, U, tid, T); break;
   }
 }
 
