@@ -376,6 +376,9 @@ sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStr
   if (p.flags & kPassHasTC) {
     if (s->dt != SV_C64 || p.m != kTcTileM || batch != 1 || p.nvec != 1)
       return set_error(SV_EINVAL, "internal: tensor-core tile pass needs one complex64 vector and 12-qubit tiles");
+    // passes of split-BF16 tensor-core blocks only: the pipelined kernel
+    if (host && ((p.flags >> 9) & 3) == SV_PREC_TC_BF16X3 && tcp_pass_ok(p, *host))
+      return launch_tile_tcp(s, p, *host, stream);
     return launch_tile_tc(s, p, stream);
   }
   const size_t smem = tile_smem(s->dt, p.m, (int)p.nvec);

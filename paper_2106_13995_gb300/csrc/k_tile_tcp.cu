@@ -1,0 +1,351 @@
+// K9: pipelined tile passes of tensor-core blocks (complex64, 12-qubit
+// tiles, split-BF16).
+//
+// Every block of such a pass is a dense 5-qubit block (smaller uncontrolled
+// blocks are padded to 5 qubits with idle tile qubits on the host): on a
+// 4096-amplitude tile it is one M = 128, N = 64, K = 64 real GEMM against the
+// embedding of U, done as A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32
+// accumulation in TMEM (paper Sec. II: a circuit moment is a matrix applied
+// to the state vector).  The kernel is arranged so that HBM, the tensor
+// cores and the CUDA cores work at the same time:
+//   - one persistent CTA per SM runs three independent groups of four
+//     warps; each group owns 128 TMEM columns (A_hi, A_lo, D), one
+//     shared-memory tile buffer, and walks its own sequence of tiles;
+//   - a group loads its next tile into registers (16 x 16 bytes a thread)
+//     while it works on the current one, and writes them to shared memory
+//     after storing the current tile, so every group keeps a tile in flight;
+//   - the B operands of all blocks of the pass are copied into shared memory
+//     once per CTA and stay there for all its tiles;
+//   - while one group waits for its MMAs the others gather, split and
+//     scatter.
+// The tile's shared-memory layout keeps each even/odd amplitude pair
+// together (16-byte units) and XORs slot bits 1..3 with tile bits 4..6 and
+// 8..10, so unit loads and stores are conflict-free and a warp's gathers of
+// one member from 32 groups spread over the banks (the host picks which tile
+// bits the lane bits address, TileOp.tbpos).  When tile bit 0 is a target it
+// is the block's first target, and members are gathered in 16-byte pairs.
+//
+// Every wait is bounded: a wait that runs out raises the error flag, the
+// group stops, and before the CTA exits it waits (bounded) for its MMAs and
+// copies and frees its TMEM.
+#include <algorithm>
+#include <cstring>
+
+#include "tile_ops.cuh"
+
+namespace sv {
+
+constexpr int kPGroups = 3;                          // tile groups per CTA
+constexpr uint32_t kPGroupThreads = 128;             // group thread t <-> TMEM lane t
+constexpr int kPThreads = kPGroups * (int)kPGroupThreads;
+constexpr uint32_t kPTileBytes = (1u << kTcTileM) * 8;   // 32 KB
+constexpr uint32_t kPBBytes = 2 * 64 * 64 * 2;       // B_hi + B_lo, BF16: 16 KB per block
+constexpr uint32_t kPUnits = (1u << kTcTileM) / 2 / kPGroupThreads;   // 16-byte units per thread
+constexpr uint32_t kPTmemCols = 512;                 // 128 per group, allocated as a power of two
+constexpr uint32_t kPSpin = 1u << 22;
+
+// shared memory: [tile buffers][B: ntc blocks][mbarriers][TMEM address, flags]
+__host__ __device__ constexpr uint32_t tcp_bars_off(int ntc) {
+  return kPGroups * kPTileBytes + (uint32_t)ntc * kPBBytes;
+}
+__host__ __device__ constexpr uint32_t tcp_smem_bytes(int ntc) {
+  return tcp_bars_off(ntc) + 8 * (1 + kPGroups) + 4 * (1 + kPGroups) + 4;
+}
+
+// Byte offset of tile amplitude l: pairs (2j, 2j+1) stay together, slot bits
+// 1..3 are XORed with tile bits 4..6 and 8..10 (linear over GF(2)).
+__host__ __device__ constexpr uint32_t tcp_swz(uint32_t l) {
+  return (l ^ ((((l >> 4) ^ (l >> 8)) & 7u) << 1)) * 8u;
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(g + 1), "r"(kPGroupThreads) : "memory");
+}
+__device__ __forceinline__ void sts128(uint32_t a, int4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ int4 lds128(uint32_t a) {
+  int4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];\n" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void tmem_st16x(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+// D (TMEM) += A (TMEM) x B (shared memory), BF16 inputs, FP32 accumulation
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+      "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// Global offsets of a thread's units: unit i of group thread t is tile
+// amplitude l = 2 (t + 128 i); its offset is the tile's base | the thread's
+// part | the trip's part, the trip parts shared by all threads (a table in
+// shared memory).
+struct TcpAddr {
+  uint64_t thr;                 // thread part of the offset
+  const uint64_t *trip;         // kPUnits trip parts
+};
+
+__device__ __forceinline__ void tcp_prefetch(const TilePass &P, uint64_t tbase, const TcpAddr &A,
+                                             int4 (&r)[kPUnits]) {
+  const int4 *g0 = reinterpret_cast<const int4 *>(P.v0);   // 16-byte units: offset / 2
+#pragma unroll
+  for (uint32_t i = 0; i < kPUnits; i++) r[i] = __ldcs(g0 + ((tbase | A.thr | A.trip[i]) >> 1));
+}
+
+struct TcpGroup {
+  int g;              // group index in the CTA
+  uint32_t tid;       // thread index in the group (= TMEM lane)
+  uint32_t tmem;      // TMEM address of the group's first column (lane 0)
+  uint32_t bar_b;     // mbarrier: every B operand has landed
+  uint32_t bar_mma;   // mbarrier of this group's MMAs
+  uint32_t *flag;     // shared: the elected thread's last wait succeeded
+  bool b_ready;       // (elected thread) bar_b has been observed
+  uint32_t done;      // this group's blocks so far (mbarrier parity)
+  bool pend_mma;      // (elected thread) MMAs committed but not observed
+};
+
+// Split 16 amplitudes into BF16 hi/lo pairs and store them in this thread's
+// TMEM lane at taddr (hi) and taddr + 32 columns (lo).
+__device__ __forceinline__ void tcp_split_store(const float2 (&x)[16], uint32_t taddr) {
+  uint32_t hi[16], lo[16];
+#pragma unroll
+  for (int y = 0; y < 16; y++) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[y].x, x[y].y);
+    const float2 hf = __bfloat1622float2(hb);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[y].x - hf.x, x[y].y - hf.y);
+    hi[y] = *reinterpret_cast<const uint32_t *>(&hb);
+    lo[y] = *reinterpret_cast<const uint32_t *>(&lb);
+  }
+  tmem_st16x(taddr, hi);
+  tmem_st16x(taddr + 32, lo);
+}
+
+// One tensor-core block on the tile at shared address `ts`, its B operand at
+// shared address `bs`.  Returns false if a wait ran out (uniform in the group).
+__device__ __forceinline__ bool tcp_block(const TileOp &op, uint32_t ts, uint32_t bs, TcpGroup &G, uint32_t *err) {
+  uint32_t soff[32];
+  soff[0] = 0;
+#pragma unroll
+  for (int q = 0; q < 5; q++) {
+    const uint32_t e = tcp_swz(1u << op.t[q]);
+#pragma unroll
+    for (int y = 0; y < (1 << q); y++) soff[y + (1 << q)] = soff[y] ^ e;
+  }
+  const uint32_t s0 = tcp_swz(thread_l(G.tid, op));   // this thread's row (group of 32 amplitudes)
+  const uint32_t lane = (G.tid & ~31u) << 16;         // the warp's TMEM lane quadrant
+  const bool pairs = op.t[0] == 0;                    // member pairs (y, y + 1) share a 16-byte unit
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    float2 x[16];
+    if (pairs) {
+#pragma unroll
+      for (int y = 0; y < 16; y += 2) {
+        const int4 v = lds128(ts + (s0 ^ soff[16 * h + y]));
+        x[y] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
+        x[y + 1] = make_float2(__int_as_float(v.z), __int_as_float(v.w));
+      }
+    } else {
+#pragma unroll
+      for (int y = 0; y < 16; y++) x[y] = lds_c(ts + (s0 ^ soff[16 * h + y]), (const float2 *)nullptr);
+    }
+    tcp_split_store(x, G.tmem + lane + 16 * h);
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+  tc_fence_before();
+  group_sync(G.g);
+  if (G.tid == 0) {
+    tc_fence_after();
+    bool ok = G.b_ready || mbar_wait(G.bar_b, 0, kPSpin);
+    G.b_ready = ok;
+    if (ok) {
+      const uint32_t idesc = instr_desc(1u);   // BF16 A and B, FP32 D, M = 128, N = 64
+      const uint32_t as[3] = {0, 0, 32}, bo[3] = {0, kPBBytes / 2, 0};
+#pragma unroll
+      for (int t = 0; t < 3; t++)
+#pragma unroll
+        for (uint32_t k = 0; k < 4; k++)
+          mma_bf16_ta(G.tmem + 64, G.tmem + as[t] + 8 * k, smem_desc(bs + bo[t] + k * 2048, 1024, 128), idesc,
+                      (t > 0 || k > 0) ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(G.bar_mma)
+                   : "memory");
+      G.pend_mma = true;
+      ok = mbar_wait(G.bar_mma, G.done & 1, kPSpin);
+      if (ok) G.pend_mma = false;
+    }
+    if (!ok) atomicExch(err, 1u);
+    *G.flag = ok ? 1u : 0u;
+  }
+  group_sync(G.g);
+  if (!*G.flag) return false;
+  G.done++;
+  tc_fence_after();
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    uint32_t r[32];
+    tmem_ld32(G.tmem + lane + 64 + 32 * h, r);
+    if (pairs) {
+#pragma unroll
+      for (int y = 0; y < 16; y += 2)
+        sts128(ts + (s0 ^ soff[16 * h + y]),
+               make_int4((int)r[2 * y], (int)r[2 * y + 1], (int)r[2 * y + 2], (int)r[2 * y + 3]));
+    } else {
+#pragma unroll
+      for (int y = 0; y < 16; y++)
+        sts_c(ts + (s0 ^ soff[16 * h + y]), make_float2(__uint_as_float(r[2 * y]), __uint_as_float(r[2 * y + 1])));
+    }
+  }
+  tc_fence_before();   // the next block's A stores and MMAs come after a group barrier
+  return true;
+}
+
+__global__ void __launch_bounds__(kPThreads, 1) k_tile_tcp(const __grid_constant__ TilePass P) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t s_trip[kPUnits];
+  const int g = (int)(threadIdx.x / kPGroupThreads);
+  const int ntc = P.nops;   // every op of the pass is a tensor-core block
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bbase = sbase + kPGroups * kPTileBytes;
+  const uint32_t bars = sbase + tcp_bars_off(ntc);
+  uint32_t *slots = reinterpret_cast<uint32_t *>(smem + tcp_bars_off(ntc) + 8 * (1 + kPGroups));
+  TcpGroup G;
+  G.g = g;
+  G.tid = threadIdx.x % kPGroupThreads;
+  G.bar_b = bars;
+  G.bar_mma = bars + 8 * (1 + g);
+  G.flag = slots + 1 + g;
+  G.b_ready = false;
+  G.done = 0;
+  G.pend_mma = false;
+  const uint32_t segmask = (1u << P.L) - 1;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 1 + kPGroups; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bars + 8 * i));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (threadIdx.x < kPUnits) {
+    const uint32_t lt = threadIdx.x * kPGroupThreads * 2;
+    s_trip[threadIdx.x] = (lt & segmask) | spread_hi(P, lt & ~segmask);
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slots)),
+                 "r"(kPTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  G.tmem = slots[0] + 128u * (uint32_t)g;
+  const uint64_t ntiles = 1ull << (P.n - P.m);
+  const uint64_t stride = (uint64_t)gridDim.x * kPGroups;
+  uint64_t t = (uint64_t)blockIdx.x * kPGroups + g;
+  // the B operands of every block of the pass, once per CTA
+  if (threadIdx.x == 0 && ntc > 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bars), "r"(ntc * kPBBytes)
+                 : "memory");
+    for (int j = 0; j < ntc; j++) {
+      const char *src = static_cast<const char *>(P.mats) + (size_t)P.ops[j].mat * sizeof(float2);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+              bbase + (uint32_t)j * kPBBytes),
+          "l"(src), "r"(kPBBytes), "r"(bars)
+          : "memory");
+    }
+  }
+  const uint32_t ts = sbase + (uint32_t)g * kPTileBytes;
+  const uint32_t lthr = G.tid * 2;
+  const TcpAddr A{(lthr & segmask) | spread_hi(P, lthr & ~segmask), s_trip};
+  int4 pf[kPUnits];
+  uint64_t tb = t < ntiles ? tile_base(P, t) : 0;
+  if (t < ntiles) tcp_prefetch(P, tb, A, pf);
+  bool failed = false;
+  for (; t < ntiles && !failed; t += stride) {
+    // the prefetched tile into the buffer (its last tile was stored before the
+    // barrier that ended the previous iteration)
+#pragma unroll
+    for (uint32_t i = 0; i < kPUnits; i++) sts128(ts + tcp_swz((G.tid + i * kPGroupThreads) * 2), pf[i]);
+    const uint64_t cur = tb;
+    if (t + stride < ntiles) {
+      tb = tile_base(P, t + stride);
+      tcp_prefetch(P, tb, A, pf);   // in flight while this tile's blocks run
+    }
+    for (int oi = 0; oi < P.nops && !failed; oi++) {
+      group_sync(g);
+      if (!tcp_block(P.ops[oi], ts, bbase + (uint32_t)oi * kPBBytes, G, P.err)) failed = true;
+    }
+    group_sync(g);
+    if (failed) break;
+    int4 *g0 = reinterpret_cast<int4 *>(P.v0);
+#pragma unroll
+    for (uint32_t i = 0; i < kPUnits; i++)
+      __stcs(g0 + ((cur | A.thr | A.trip[i]) >> 1), lds128(ts + tcp_swz((G.tid + i * kPGroupThreads) * 2)));
+    group_sync(g);
+  }
+  // no copy or MMA may outlive the CTA
+  if (G.tid == 0) {
+    if (G.pend_mma) mbar_wait(G.bar_mma, G.done & 1, kPSpin);
+    if (g == 0 && ntc > 0) mbar_wait(G.bar_b, 0, kPSpin);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(slots[0]), "r"(kPTmemCols));
+}
+
+// Thread-index bits of a block's rows (host): the lane bits first take tile
+// bits that reach distinct bank groups under tcp_swz -- with 8-byte gathers
+// one bit from each of the classes {0}, {1,4,8}, {2,5,9}, {3,6,10}; with
+// 16-byte pair gathers (tile bit 0 a target) one from each of the last three
+// -- then the remaining free bits follow in increasing order.
+void tcp_row_positions(TileOp &op) {
+  uint32_t targets = 0;
+  for (int j = 0; j < op.k; j++) targets |= 1u << op.t[j];
+  static const int kClass[4][3] = {{0, -1, -1}, {1, 4, 8}, {2, 5, 9}, {3, 6, 10}};
+  int P[12], np = 0;
+  uint32_t used = targets;
+  for (int c = (targets & 1u) ? 1 : 0; c < 4; c++)
+    for (int p : kClass[c])
+      if (p >= 0 && !((used >> p) & 1u)) {
+        P[np++] = p;
+        used |= 1u << p;
+        break;
+      }
+  for (int p = 0; p < kTcTileM; p++)
+    if (!((used >> p) & 1u)) {
+      P[np++] = p;
+      used |= 1u << p;
+    }
+  std::memset(op.tbpos, 0, sizeof(op.tbpos));
+  for (int i = 0; i < np && i < 9; i++) op.tbpos[i >> 1] |= (uint8_t)(P[i] << (4 * (i & 1)));
+}
+
+bool tcp_pass_ok(const TilePass &p, const HostPass &host) {
+  if (p.m != kTcTileM || p.nops < 1 || p.nops > kTcpMaxBlocks) return false;
+  for (int i = 0; i < p.nops; i++)
+    if (host.ops[i].kind != TOP_TC || host.ops[i].k != 5) return false;
+  return true;
+}
+
+sv_status launch_tile_tcp(sv_state *s, const TilePass &p, const HostPass &host, cudaStream_t stream) {
+  if (!tcp_pass_ok(p, host)) return set_error(SV_EINVAL, "internal: not a pure tensor-core tile pass");
+  SV_TRY(func_attr_once((const void *)k_tile_tcp, s->device, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                        (int)tcp_smem_bytes(kTcpMaxBlocks)));
+  const uint64_t ntiles = 1ull << (p.n - p.m);
+  const uint64_t per_cta = (uint64_t)kPGroups;
+  const int grid = (int)std::min<uint64_t>((ntiles + per_cta - 1) / per_cta, (uint64_t)s->sm_count);
+  k_tile_tcp<<<grid, kPThreads, tcp_smem_bytes(p.nops), stream>>>(p);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+}  // namespace sv

@@ -136,6 +136,7 @@ static uint64_t qmask(const std::vector<int> &v) {
 }
 
 static int mat_entries(const Block &b) {
+  if (b.kind == TOP_TC) return 1024;   // a 5-qubit block (its packed operand is counted as 32 x 32)
   if (b.kind != TOP_DENSE && b.kind != TOP_DIAG) return 0;
   const int d = 1 << (int)b.qubits.size();
   return b.diag ? d : d * d;

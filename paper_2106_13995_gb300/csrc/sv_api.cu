@@ -240,10 +240,29 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
         }
       }
     } else if (op.kind == TOP_TC) {
+      // targets in increasing tile position (tile bit 0, if a target, is the
+      // first: the pipelined kernel then gathers member pairs), U permuted
+      // to match; rows of the GEMM on the free tile bits, lane bits chosen
+      // to spread a warp's gathers over the banks
+      int ord[6] = {0, 1, 2, 3, 4, 5};
+      std::sort(ord, ord + op.k, [&](int a, int c) { return op.t[a] < op.t[c]; });
+      uint8_t tsorted[6];
+      for (int j = 0; j < op.k; j++) tsorted[j] = op.t[ord[j]];
+      for (int j = 0; j < op.k; j++) op.t[j] = tsorted[j];
+      const int d = 1 << op.k;
+      std::vector<cd> Up((size_t)d * d);
+      auto from_sorted = [&](int x) {
+        int y = 0;
+        for (int j = 0; j < op.k; j++) y |= ((x >> j) & 1) << ord[j];
+        return y;
+      };
+      for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++) Up[(size_t)r * d + c] = blk.U[(size_t)from_sorted(r) * d + from_sorted(c)];
+      tcp_row_positions(op);
       while (prog.mats.size() % 16) prog.mats.push_back(0);
       op.mat = (uint32_t)(prog.mats.size() / ab);
       std::vector<uint32_t> packed;
-      tc_pack_matrix(blk.U, (sv_prec)b.prec, packed);
+      tc_pack_matrix(Up, (sv_prec)b.prec, packed);
       const uint8_t *pb = reinterpret_cast<const uint8_t *>(packed.data());
       prog.mats.insert(prog.mats.end(), pb, pb + packed.size() * 4);
       tp.flags |= kPassHasTC | ((uint32_t)b.prec << 9);
@@ -350,6 +369,26 @@ sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &
 
 static ProgCache<CachedProgram> g_cache(kProgramCacheDefault);
 
+// Pad a block of k < 5 qubits to a 5-qubit block U' = I (x) U over idle
+// qubits of its pass's tile (tile qubits S, tile position p <-> S[p]): tile
+// positions 7 and 11, which do not steer the pipelined kernel's bank
+// mapping, first, then the highest free ones.
+static void pad_in_tile(Block &blk, const std::vector<int> &S) {
+  static const int kOrder[12] = {7, 11, 10, 9, 8, 6, 5, 4, 3, 2, 1, 0};
+  const int k = (int)blk.qubits.size(), d = 1 << k;
+  for (int p : kOrder) {
+    if ((int)blk.qubits.size() == 5) break;
+    if (p >= (int)S.size()) continue;
+    if (std::find(blk.qubits.begin(), blk.qubits.end(), S[p]) == blk.qubits.end()) blk.qubits.push_back(S[p]);
+  }
+  std::vector<cd> U5(32 * 32, 0.0);
+  for (int r = 0; r < 32; r++)
+    for (int c = 0; c < 32; c++)
+      if ((r >> k) == (c >> k)) U5[(size_t)r * 32 + c] = blk.U[(size_t)(r & (d - 1)) * d + (c & (d - 1))];
+  blk.U = std::move(U5);
+  blk.diag = false;
+}
+
 static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gates, const Opts &o,
                                        CachedProgram &out) {
   out.blocks = fuse(gates, o.fusion_k);
@@ -357,7 +396,7 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
   int m = o.tile_m, L = o.L;
   if (!fit_tile(out.blocks, s->n, lmin(s->dt), mmax(s->dt, 1), m, L))
     return set_error(SV_EUNSUPPORTED, "a fused block does not fit a shared-memory tile");
-  if (o.prec == SV_PREC_PLAIN && o.fusion_k >= 2 && m < s->n) {
+  if (o.fusion_k >= 2 && m < s->n) {
     // blocks that meet inside a pass merge (one pass-sized op instead of two)
     const std::vector<PassPlan> first = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, kMaxMatPerPass);
     if (!first.empty()) {
@@ -389,13 +428,29 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
     blk.qubits.push_back(extra);
   };
   if (tc && m == kTcTileM && o.tc_in_tile) {
+    // Split-BF16: every uncontrolled dense or diagonal block of at most 5
+    // qubits runs on the tensor cores (padded to 5 qubits with idle tile
+    // qubits once its pass is known), so most passes hold tensor-core blocks
+    // only and take the pipelined kernel; at most kTcpMaxBlocks per pass,
+    // whose operands stay in shared memory (each counts 1024 entries).
+    // Split-TF32: dense 4- and 5-qubit blocks only.
+    const bool bf16 = o.prec == SV_PREC_TC_BF16X3;
     for (Block &blk : out.blocks) {
-      pad4(blk);
-      if (blk.kind == TOP_DENSE && blk.qubits.size() == 5 && blk.controls.empty() && !blk.diag) blk.kind = TOP_TC;
+      if (bf16) {
+        if (blk.kind == TOP_DENSE && blk.controls.empty() && blk.qubits.size() <= 5) blk.kind = TOP_TC;
+      } else {
+        pad4(blk);
+        if (blk.kind == TOP_DENSE && blk.qubits.size() == 5 && blk.controls.empty() && !blk.diag) blk.kind = TOP_TC;
+      }
     }
-    std::vector<PassPlan> passes = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, kMaxMatPerPass);
+    const int mat_cap = bf16 ? kTcpMaxBlocks * 1024 + 1023 : kMaxMatPerPass;
+    std::vector<PassPlan> passes = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, mat_cap);
     if (passes.empty() && !out.blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
-    for (const PassPlan &P : passes) SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
+    for (PassPlan &P : passes) {
+      for (Block &blk : P.ops)
+        if (blk.kind == TOP_TC && blk.qubits.size() < 5) pad_in_tile(blk, P.S);
+      SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
+    }
     out.lay = layout_of(out.prog, 0, 0);
     return SV_OK;
   }

@@ -430,6 +430,14 @@ struct HostPass {
 sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream,
                               const HostPass *host = nullptr);
 sv_status launch_tile_tc(sv_state *s, const TilePass &p, cudaStream_t stream);   // k_tile_tc.cu
+// pipelined split-BF16 tile pass (k_tile_tcp.cu): at most kTcpMaxBlocks
+// tensor-core blocks per pass, whose B operands stay in shared memory
+constexpr int kTcpMaxBlocks = 6;
+sv_status launch_tile_tcp(sv_state *s, const TilePass &p, const HostPass &host, cudaStream_t stream);
+// a pass the pipelined kernel runs: 12-qubit tiles, 1..kTcpMaxBlocks ops, all 5-qubit TOP_TC
+bool tcp_pass_ok(const TilePass &p, const HostPass &host);
+// plan-time row map of a TOP_TC op for the pipelined kernel's bank layout
+void tcp_row_positions(TileOp &op);
 // tensor-core 5-qubit block (k_tc.cu)
 size_t tc_matrix_words(sv_prec mode);
 void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t> &out);

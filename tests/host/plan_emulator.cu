@@ -301,3 +301,148 @@ extern "C" int cache_selftest(const sv_circuit *const *cs, int nc, int limit) {
   sv_program_cache_limit(old);
   return rc;
 }
+
+// The split-BF16 tensor-core program the library builds for a circuit
+// (through its own cache and planner on a host-only state handle), run on
+// the CPU in complex128: every tensor-core block's packed operand (BF16 hi
+// and lo parts of the real embedding, in the tensor cores' core-matrix
+// layout) is unpacked back to its complex 32 x 32 matrix and applied on the
+// block's 5 tile positions; CUDA-core blocks use their stored matrices.
+// Also checks what the pipelined kernel relies on: 5 targets in increasing
+// tile position, a row map that is a bijection onto the free tile bits,
+// lane bits on distinct bank classes.  Returns the number of passes and sets
+// *npure to the passes the pipelined kernel takes, or -1 (message printed).
+static float bf16_at(const uint8_t *part, int n, int k) {
+  // canonical K-major layout without swizzle, 2-byte elements, 64 rows:
+  // core matrices of 8 rows x 16 bytes, 64 * 16 bytes apart along K and 128
+  // bytes apart along the rows
+  const uint32_t o = (uint32_t)(k / 8) * 64 * 16 + (uint32_t)(n / 8) * 128 + (uint32_t)(n % 8) * 16 +
+                     (uint32_t)(k % 8) * 2;
+  uint16_t h;
+  std::memcpy(&h, part + o, 2);
+  const uint32_t bits = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &bits, 4);
+  return f;
+}
+extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure) {
+  typedef std::complex<double> cx;
+  sv_state st;
+  st.n = c->n_qubits;
+  st.dt = SV_C64;
+  sv_options opt{0, 0, SV_PREC_TC_BF16X3, SV_MODE_TILED, 0};
+  ProgramRef cp;
+  Opts o;
+  if (get_program(&st, c, nullptr, &opt, &cp, &o) != SV_OK) {
+    std::printf("get_program: %s\n", sv_last_error());
+    return -1;
+  }
+  const DeviceProgram &prog = cp->prog;
+  const int n = c->n_qubits;
+  cx *psi = reinterpret_cast<cx *>(psi_);
+  *npure = 0;
+  for (size_t pi = 0; pi < prog.passes.size(); pi++) {
+    const TilePass &tp = prog.passes[pi];
+    if (tp.flags & kPassTC) {
+      std::printf("unexpected tensor-core pass of its own\n");
+      return -1;
+    }
+    const HostPass hp{prog.ops.data() + cp->op0s[pi], prog.mats.data()};
+    *npure += tcp_pass_ok(tp, hp) ? 1 : 0;
+    const uint32_t TS = 1u << tp.m;
+    // decode every op's matrix once
+    std::vector<std::vector<cx>> Us(tp.nops);
+    for (int oi = 0; oi < tp.nops; oi++) {
+      const TileOp &op = prog.ops[cp->op0s[pi] + oi];
+      const int D = 1 << op.k;
+      std::vector<cx> &U = Us[oi];
+      const uint8_t *base = prog.mats.data() + (size_t)op.mat * 8;
+      if (op.kind == TOP_TC) {
+        if (op.k != 5) { std::printf("tensor-core block with %d targets\n", op.k); return -1; }
+        uint32_t tmask = 0;
+        for (int j = 0; j < 5; j++) {
+          if (j > 0 && op.t[j] <= op.t[j - 1]) { std::printf("targets not increasing\n"); return -1; }
+          tmask |= 1u << op.t[j];
+        }
+        uint32_t rows = 0;
+        for (int i = 0; i < 7; i++) rows |= 1u << ((op.tbpos[i >> 1] >> (4 * (i & 1))) & 15u);
+        if ((rows | tmask) != (1u << tp.m) - 1 || (rows & tmask)) { std::printf("row map not a bijection\n"); return -1; }
+        U.assign(32 * 32, 0.0);
+        const uint8_t *hi = base, *lo = base + 64 * 64 * 2;
+        for (int r = 0; r < 32; r++)
+          for (int q = 0; q < 32; q++) {
+            const double re = (double)bf16_at(hi, 2 * r, 2 * q) + (double)bf16_at(lo, 2 * r, 2 * q);
+            const double im = (double)bf16_at(hi, 2 * r + 1, 2 * q) + (double)bf16_at(lo, 2 * r + 1, 2 * q);
+            U[(size_t)r * 32 + q] = cx(re, im);
+          }
+      } else if (op.kind == TOP_DIAG) {
+        const float *f = reinterpret_cast<const float *>(base);
+        U.resize(D);
+        for (int r = 0; r < D; r++) U[r] = cx(f[2 * r], f[2 * r + 1]);
+      } else if (op.kind == TOP_DENSE) {
+        const float *f = reinterpret_cast<const float *>(base);
+        U.assign((size_t)D * D, 0.0);
+        if (op.k <= 3) {   // row pairs
+          for (int p = 0; p < D / 2; p++)
+            for (int y = 0; y < D; y++) {
+              const float *q = f + 4 * ((size_t)p * D + y);
+              U[(size_t)(2 * p) * D + y] = cx(q[0], q[2]);
+              U[(size_t)(2 * p + 1) * D + y] = cx(q[1], q[3]);
+            }
+        } else {
+          for (int e = 0; e < D * D; e++) U[e] = cx(f[2 * e], f[2 * e + 1]);
+        }
+      } else {
+        std::printf("unexpected op kind %d\n", op.kind);
+        return -1;
+      }
+    }
+    for (uint64_t t = 0; t < (1ull << (n - tp.m)); t++) {
+      uint64_t gbase = 0;
+      for (int j = 0; j < n - tp.m; j++) gbase |= ((t >> j) & 1ull) << tp.out_pos[j];
+      std::vector<uint64_t> gi(TS);
+      for (uint32_t l = 0; l < TS; l++) {
+        uint64_t g = l & ((1u << tp.L) - 1);
+        for (int b = tp.L; b < tp.m; b++) g |= (uint64_t)((l >> b) & 1u) << tp.hi_pos[b - tp.L];
+        gi[l] = gbase | g;
+      }
+      std::vector<cx> v(TS);
+      for (uint32_t l = 0; l < TS; l++) v[l] = psi[gi[l]];
+      for (int oi = 0; oi < tp.nops; oi++) {
+        const TileOp &op = prog.ops[cp->op0s[pi] + oi];
+        const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);
+        if ((gbase & gcm) != gcm) continue;
+        const std::vector<cx> &U = Us[oi];
+        const int K = op.k, D = 1 << K;
+        if (op.kind == TOP_DIAG) {
+          for (uint32_t g = 0; g < (TS >> __builtin_popcount(op.lcmask)); g++) {
+            const uint32_t l = ins0_mask_h(g, op.lcmask) | op.lcmask;
+            uint32_t r = 0;
+            for (int j = 0; j < K; j++) r |= ((l >> op.t[j]) & 1u) << j;
+            v[l] = U[r] * v[l];
+          }
+          continue;
+        }
+        std::vector<uint32_t> off(D);
+        for (int y = 0; y < D; y++) {
+          uint32_t ofs = 0;
+          for (int j = 0; j < K; j++) ofs |= (uint32_t)((y >> j) & 1) << op.t[j];
+          off[y] = ofs;
+        }
+        const uint32_t fixed = off[D - 1] | op.lcmask;
+        for (uint32_t g = 0; g < (TS >> __builtin_popcount(fixed)); g++) {
+          const uint32_t i0 = ins0_mask_h(g, fixed) | op.lcmask;
+          std::vector<cx> x(D);
+          for (int y = 0; y < D; y++) x[y] = v[i0 + off[y]];
+          for (int r = 0; r < D; r++) {
+            cx a = 0;
+            for (int y = 0; y < D; y++) a += U[(size_t)r * D + y] * x[y];
+            v[i0 + off[r]] = a;
+          }
+        }
+      }
+      for (uint32_t l = 0; l < TS; l++) psi[gi[l]] = v[l];
+    }
+  }
+  return (int)prog.passes.size();
+}

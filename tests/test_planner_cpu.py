@@ -143,3 +143,30 @@ def test_program_cache_eviction_keeps_held_programs(emu):
     assert emu.cache_selftest(arr, len(ms), 8) == 0
     # a bound larger than the number of circuits: nothing is evicted
     assert emu.cache_selftest(arr, 5, 64) == 0
+
+
+def test_split_bf16_programs_match_oracle(emu, oracle):
+    """The split-BF16 tensor-core programs: small blocks padded to 5 qubits
+    with idle tile qubits, targets in increasing tile position with the
+    matrix permuted to match, operands packed as BF16 hi/lo parts of the
+    real embedding.  Unpacked and run on the CPU they reproduce the FP64
+    oracle to the split's precision (hi + lo keeps about 16 significant
+    bits per entry); circuits without controlled gates take the pipelined
+    kernel in every pass."""
+    from paper_2106_13995_gb300 import sim
+    emu.tc_program_emulate.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+    cases = [(W.grid_random(3, 5, 10, 1), True), (W.random_u3_cz(14, 8, 3), True),
+             (W.remove_qubits(W.grid_random(5, 6, 6, 2), 16, 7), True), (W.multiplier(3), False)]
+    for c, pure in cases:
+        mm = sim.marshal(c)
+        psi = np.zeros(1 << c.n_qubits, dtype=np.complex128)
+        psi[0] = 1
+        npure = C.c_int()
+        npass = emu.tc_program_emulate(C.addressof(mm.c), psi.ctypes.data, C.byref(npure))
+        assert npass > 0, c.name
+        if pure:
+            assert npure.value == npass, (c.name, npure.value, npass)
+        want = oracle.run(c)
+        inf = oracle.infidelity(want, psi)
+        assert inf <= 1e-8, (c.name, inf)
+        assert np.max(np.abs(psi - want)) <= 1e-4 * np.max(np.abs(want)), c.name
