@@ -39,8 +39,32 @@ import workloads as W  # noqa: E402
 
 METRIC = "gates/s + HBM GB/s at 30q vs roofline; adjoint grads/s batched vs plain"
 UNIT = "gates/s"
-TILE_KERNEL_SRC = [os.path.join(ROOT, "paper_2106_13995_gb300", "csrc", f) for f in ("k_tile.cu", "tile_ops.cuh")]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tile_traffic.json")
+CSRC = os.path.join(ROOT, "paper_2106_13995_gb300", "csrc")
+# the dominant kernel of each arithmetic mode, its sources and its ncu traffic record
+KERNELS = {
+    "plain": ("k_tile_inl (tile pass; op list and 1-3 qubit matrices in the parameter block)",
+              ["k_tile.cu", "tile_ops.cuh"], "k_tile_traffic.json"),
+    "bf16x3": ("k_tile_tcp (pipelined tile pass of split-BF16 tensor-core blocks)",
+               ["k_tile_tcp.cu", "tile_ops.cuh"], "k_tile_tcp_traffic.json"),
+    "tf32x3": ("k_tile_inl and k_dense_tc (tile passes and tensor-core passes)", [], None),
+}
+
+
+def traffic_of(prec: str, n: int):
+    """DRAM bytes per launch from the ncu record, if it was taken on the
+    current sources of the kernel and for this width; else None."""
+    _, srcs, rec = KERNELS[prec]
+    if not rec:
+        return None
+    try:
+        with open(os.path.join(ROOT, "profiles", rec)) as f:
+            tr = json.load(f)
+        h = hashlib.sha256(b"".join(open(os.path.join(CSRC, x), "rb").read() for x in srcs)).hexdigest()[:16]
+        if tr.get("k_tile_sha") == h and tr.get("n_qubits") == n:
+            return tr["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
 
 
 def parse():
@@ -51,10 +75,11 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--qubits", type=int, default=30,
                     help="30 = the 5x6 grid; fewer = the same grid with random qubits removed")
-    ap.add_argument("--prec", choices=("plain", "bf16x3", "tf32x3"), default="plain",
-                    help="arithmetic of the main step's fused blocks (tensor-core modes fuse 5-qubit blocks)")
+    ap.add_argument("--prec", choices=("plain", "bf16x3", "tf32x3"), default="bf16x3",
+                    help="arithmetic of the main step's fused blocks: split-BF16 tensor-core blocks "
+                         "(default), plain FP32 on CUDA cores, or split-TF32")
     ap.add_argument("--sections", default="all",
-                    help="comma list of step,e2e,roofline,tc,mult,single,adjoint,uneven,widths,cpu (default all)")
+                    help="comma list of step,e2e,roofline,firstcall,tc,mult,single,adjoint,uneven,widths,cpu (default all)")
     return ap.parse_args()
 
 
@@ -86,6 +111,15 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
         return 6800.0, "fallback (6.8 TB/s)"
+
+
+def measured_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except Exception:
+        return 1900.0, "fallback (1.9 PFLOP/s bf16 burst)"
 
 
 # ---------------------------------------------------------------------------
@@ -282,7 +316,7 @@ def main():
     from paper_2106_13995_gb300 import sim
 
     sections = set(args.sections.split(",")) if args.sections != "all" else \
-        {"step", "e2e", "roofline", "tc", "mult", "single", "adjoint", "uneven", "widths", "cpu"}
+        {"step", "e2e", "roofline", "firstcall", "tc", "mult", "single", "adjoint", "uneven", "widths", "cpu"}
     circ = workload(args.qubits)
     n = circ.n_qubits
     m = sim.marshal(circ)
@@ -324,6 +358,11 @@ def main():
            "data": "synthetic", "config": config_of(circ, args)}
     nblocks, npasses = state.plan_info(m, opts=step_opts)
     out["config"]["prec"] = args.prec
+    out["config"]["arithmetic"] = {
+        "bf16x3": "complex64 state; fused blocks of up to 5 qubits on the tensor cores as split-BF16 "
+                  "(hi*hi + hi*lo + lo*hi), FP32 accumulation",
+        "plain": "complex64 state; fused blocks of up to 3 qubits in FP32 on the CUDA cores",
+        "tf32x3": "complex64 state; 5-qubit blocks on the tensor cores as split-TF32, FP32 accumulation"}[args.prec]
     out["config"]["fused_blocks"] = nblocks
     out["config"]["tile_passes"] = npasses
 
@@ -383,38 +422,71 @@ def main():
         tc = timed(lambda: state.apply_circuit(m, opts=step_opts), reps) / reps
         per_launch = tc / npasses
         achieved = gate_bytes / per_launch / 1e9
-        traffic = None
-        try:
-            with open(TRAFFIC_FILE) as f:
-                tr = json.load(f)
-            src_hash = hashlib.sha256(b"".join(open(f, "rb").read() for f in TILE_KERNEL_SRC)).hexdigest()[:16]
-            if tr.get("k_tile_sha") == src_hash and tr.get("n_qubits") == n:
-                traffic = tr["dram_bytes_per_launch"]
-        except Exception:
-            traffic = None
-        kernel = {"plain": "k_tile_inl (tile pass; op list and 1-3 qubit matrices in the parameter block)",
-                  "bf16x3": "k_tile_tc (tile pass with tensor-core 5-qubit blocks)",
-                  "tf32x3": "k_tile_inl and k_dense_tc (tile passes and tensor-core passes)"}[args.prec]
-        if args.prec != "plain":
-            traffic = None    # the stored capture is of the plain tile pass
         out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                           "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+                           "frac": achieved / peak, "traffic": traffic_of(args.prec, n),
+                           "kernel": KERNELS[args.prec][0],
                            "algorithmic_bytes_per_launch": gate_bytes, "launches_per_circuit": npasses,
-                           "avg_launch_ms": per_launch * 1e3, "peak_source": peak_src}
-        # the same passes against the FP32 FMA rate: after fusion a pass does
-        # tens of multiply-adds per amplitude it moves, so instruction issue,
-        # not HBM, bounds it; flops = 2 x (planned multiply-adds per amplitude)
-        # x 2^n, peak = SMs x 128 FP32 lanes x 2 flops x the maximum SM clock
-        if args.prec == "plain":
-            fmas = state.plan_fmas(m, opts=step_opts)
-            flops = 2.0 * fmas * (1 << n)
-            mhz = out["clocks"].get("sm_max_mhz") or 2070.0
-            sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            alu_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
-            out["roofline_alu"] = {"bound": "alu", "achieved": flops / tc / 1e12, "peak": alu_peak,
-                                   "unit": "TFLOP/s", "frac": flops / tc / 1e12 / alu_peak,
-                                   "fma_per_amplitude": fmas, "flops_per_circuit": flops, "kernel": kernel,
-                                   "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz"}
+                           "avg_launch_ms": per_launch * 1e3, "circuit_ms": tc * 1e3, "peak_source": peak_src}
+        if args.prec == "bf16x3":
+            # the same passes against the tensor pipe: each 5-qubit block is a
+            # (2^n/32 x 64) x (64 x 64) real GEMM done as three BF16 products,
+            # 3 x 2 x 64 x 64 / 32 = 768 flops per amplitude; peak = the
+            # measured dense BF16 rate (burst)
+            fmas = state.plan_fmas(m, opts=step_opts)       # 128 per amplitude per 5-qubit block
+            flops = 3 * 2 * fmas * (1 << n)
+            tpeak, tsrc = measured_bf16()
+            out["roofline_tensor"] = {"bound": "tensor", "achieved": flops / tc / 1e12, "peak": tpeak,
+                                      "unit": "TFLOP/s", "frac": flops / tc / 1e12 / tpeak,
+                                      "flops_per_circuit": flops, "blocks": nblocks, "peak_source": tsrc}
+        # the same circuit with CUDA-core FP32 arithmetic (k_tile_inl), for comparison
+        popts = sim.options()
+        nb_p, np_p = state.plan_info(m, opts=popts)
+        state.set_basis(0)
+        state.apply_circuit(m, opts=popts)
+        tp_ = timed(lambda: state.apply_circuit(m, opts=popts), reps) / reps
+        fmas_p = state.plan_fmas(m, opts=popts)
+        mhz = out["clocks"].get("sm_max_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        out["plain_fp32"] = {"circuit_ms": tp_ * 1e3, "gates_per_s": len(circ.ops) / tp_, "passes": np_p,
+                             "blocks": nb_p, "avg_launch_ms": tp_ / np_p * 1e3,
+                             "hbm_frac": gate_bytes / (tp_ / np_p) / 1e9 / peak,
+                             "traffic": traffic_of("plain", n), "kernel": KERNELS["plain"][0],
+                             # after fusion a CUDA-core pass does tens of multiply-adds per
+                             # amplitude it moves: flops = 2 x planned multiply-adds x 2^n
+                             "alu": {"bound": "alu", "achieved": 2 * fmas_p * (1 << n) / tp_ / 1e12,
+                                     "peak": alu_peak, "unit": "TFLOP/s",
+                                     "frac": 2 * fmas_p * (1 << n) / tp_ / 1e12 / alu_peak,
+                                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz"}}
+
+    # ---- first call of a new circuit: planning, upload, first run -----------------
+    if "firstcall" in sections:
+        from paper_2106_13995_gb300 import _native as NF
+        fresh = sim.StateVector(n, "c64", device=dev)   # its own program cache entries
+        fresh.set_basis(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fresh.plan_info(m, opts=step_opts)                # fusion and pass planning only
+        t_plan = time.perf_counter() - t0
+        fresh2 = sim.StateVector(n, "c64", device=dev)
+        fresh2.set_basis(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fresh2.apply_circuit(m, opts=step_opts)           # plan + upload + run
+        torch.cuda.synchronize()
+        t_first = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fresh2.apply_circuit(m, opts=step_opts)           # cached program
+        torch.cuda.synchronize()
+        t_again = time.perf_counter() - t0
+        out["first_call"] = {"plan_ms": 1e3 * t_plan, "first_apply_ms": 1e3 * t_first,
+                             "cached_apply_ms": 1e3 * t_again,
+                             "note": "wall clock on the host around one call each; planning fuses the gates "
+                                     "(FP64 block products), plans the tile passes and packs the operands"}
+        fresh.close()
+        fresh2.close()
+        del fresh, fresh2
+        torch.cuda.empty_cache()
 
     # ---- the same circuit with fused 5-qubit blocks on the tensor cores ----------
     if "tc" in sections:
@@ -629,10 +701,10 @@ def main():
             mw = sim.marshal(cw)
             sw = sim.StateVector(nw, "c64", device=dev)
             sw.set_basis(0)
-            sw.apply_circuit(mw)
-            nbw, npw = sw.plan_info(mw)
+            sw.apply_circuit(mw, opts=step_opts)
+            nbw, npw = sw.plan_info(mw, opts=step_opts)
             kw = 3
-            tw = timed(lambda: (sw.set_basis(0), sw.apply_circuit(mw)), kw) / kw
+            tw = timed(lambda: (sw.set_basis(0), sw.apply_circuit(mw, opts=step_opts)), kw) / kw
             sweep[str(nw)] = {"gates": len(cw.ops), "passes": npw, "ms": 1e3 * tw,
                               "gates_per_s": len(cw.ops) / tw,
                               "hbm_gbs_effective": len(cw.ops) * 2 * (1 << nw) * 8 / tw / 1e9}

@@ -60,12 +60,15 @@ typedef enum {
 typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
 
 /* Arithmetic of fused dense blocks.  In the tensor-core modes the fusion
- * width defaults to 5 and every dense 4- or 5-qubit block is applied on the
- * tensor cores (complex64 states of >= 12 qubits; a 4-qubit block is padded
- * with an idle qubit).  Split-BF16 runs them inside 12-qubit tile passes
- * unless sv_options.tile_m asks for another tile size; split-TF32 runs them
- * as passes of their own unless tile_m is 12.  complex128 states always use
- * FP64 CUDA-core arithmetic. */
+ * width defaults to 5 (complex64 states of >= 12 qubits).  Split-BF16 runs
+ * inside 12-qubit tile passes unless sv_options.tile_m asks for another tile
+ * size: every uncontrolled dense or diagonal block of up to 5 qubits goes to
+ * the tensor cores, padded to 5 qubits with idle qubits of its tile, and
+ * passes made only of such blocks (at most 6) take the pipelined tensor-core
+ * kernel; blocks with controls stay on the CUDA cores.  Split-TF32 applies
+ * dense 4- and 5-qubit blocks on the tensor cores (a 4-qubit block padded
+ * with an idle qubit), as passes of their own unless tile_m is 12.
+ * complex128 states always use FP64 CUDA-core arithmetic. */
 typedef enum {
   SV_PREC_PLAIN = 0,       /* FP32 FMA on CUDA cores */
   SV_PREC_TC_BF16X3 = 1,   /* tensor cores, split-BF16 (3 products), FP32 accumulate */
@@ -195,7 +198,8 @@ sv_status sv_plan_info(sv_state *s, const sv_circuit *c, const double *params, c
  * summed over its fused blocks.  A dense k-qubit block with c controls
  * costs 4 * 2^k / 2^c (each affected amplitude takes 2^k complex
  * multiply-adds of 4 real ones), a diagonal block 4 / 2^c; blocks run on
- * the tensor cores count as dense.  This is the work the tile passes'
+ * the tensor cores count as dense blocks of the size they run at (split-BF16
+ * tile passes pad every block to 5 qubits: 128 each).  This is the work the tile passes'
  * arithmetic roofline counts (times 2^n amplitudes, 2 flops each).
  *   fma_per_amp: host pointer, receives the sum.
  * Builds and caches the plan; launches nothing.  Same errors as

@@ -58,6 +58,14 @@ __host__ __device__ constexpr uint32_t tcp_swz(uint32_t l) {
   return (l ^ ((((l >> 4) ^ (l >> 8)) & 7u) << 1)) * 8u;
 }
 
+// Per-block set-up, computed on the host and passed in the launch's
+// parameter block (warp-uniform reads): each block's member offsets
+// tcp_swz(target bits of y) and the offset contributed by each row bit.
+struct TcpTable {
+  uint32_t soff[kTcpMaxBlocks][32];
+  uint32_t rbit[kTcpMaxBlocks][8];
+};
+
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(g + 1), "r"(kPGroupThreads) : "memory");
 }
@@ -118,12 +126,16 @@ struct TcpGroup {
 // TMEM lane at taddr (hi) and taddr + 32 columns (lo).
 __device__ __forceinline__ void tcp_split_store(const float2 (&x)[16], uint32_t taddr) {
   uint32_t hi[16], lo[16];
+  const uint64_t neg1 = pk2(-1.0f, -1.0f);
 #pragma unroll
   for (int y = 0; y < 16; y++) {
     const __nv_bfloat162 hb = __floats2bfloat162_rn(x[y].x, x[y].y);
-    const float2 hf = __bfloat1622float2(hb);
-    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[y].x - hf.x, x[y].y - hf.y);
     hi[y] = *reinterpret_cast<const uint32_t *>(&hb);
+    // the hi parts back in FP32 (a BF16 is the top half of an FP32), then
+    // x - hi in one packed FMA
+    const uint64_t hf = pk2(__uint_as_float(hi[y] << 16), __uint_as_float(hi[y] & 0xFFFF0000u));
+    const float2 l = upk2(fma2(hf, neg1, pk2(x[y].x, x[y].y)));
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(l.x, l.y);
     lo[y] = *reinterpret_cast<const uint32_t *>(&lb);
   }
   tmem_st16x(taddr, hi);
@@ -132,16 +144,11 @@ __device__ __forceinline__ void tcp_split_store(const float2 (&x)[16], uint32_t 
 
 // One tensor-core block on the tile at shared address `ts`, its B operand at
 // shared address `bs`.  Returns false if a wait ran out (uniform in the group).
-__device__ __forceinline__ bool tcp_block(const TileOp &op, uint32_t ts, uint32_t bs, TcpGroup &G, uint32_t *err) {
-  uint32_t soff[32];
-  soff[0] = 0;
+__device__ __forceinline__ bool tcp_block(const TileOp &op, const uint32_t *soff, const uint32_t *rbit, uint32_t ts,
+                                          uint32_t bs, TcpGroup &G, uint32_t *err) {
+  uint32_t s0 = 0;   // this thread's row (group of 32 amplitudes)
 #pragma unroll
-  for (int q = 0; q < 5; q++) {
-    const uint32_t e = tcp_swz(1u << op.t[q]);
-#pragma unroll
-    for (int y = 0; y < (1 << q); y++) soff[y + (1 << q)] = soff[y] ^ e;
-  }
-  const uint32_t s0 = tcp_swz(thread_l(G.tid, op));   // this thread's row (group of 32 amplitudes)
+  for (int i = 0; i < 7; i++) s0 ^= ((G.tid >> i) & 1u) ? rbit[i] : 0u;
   const uint32_t lane = (G.tid & ~31u) << 16;         // the warp's TMEM lane quadrant
   const bool pairs = op.t[0] == 0;                    // member pairs (y, y + 1) share a 16-byte unit
 #pragma unroll
@@ -208,7 +215,8 @@ __device__ __forceinline__ bool tcp_block(const TileOp &op, uint32_t ts, uint32_
   return true;
 }
 
-__global__ void __launch_bounds__(kPThreads, 1) k_tile_tcp(const __grid_constant__ TilePass P) {
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_tile_tcp(const __grid_constant__ TilePass P, const __grid_constant__ TcpTable T) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_trip[kPUnits];
   const int g = (int)(threadIdx.x / kPGroupThreads);
@@ -279,7 +287,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tile_tcp(const __grid_constant
     }
     for (int oi = 0; oi < P.nops && !failed; oi++) {
       group_sync(g);
-      if (!tcp_block(P.ops[oi], ts, bbase + (uint32_t)oi * kPBBytes, G, P.err)) failed = true;
+      if (!tcp_block(P.ops[oi], T.soff[oi], T.rbit[oi], ts, bbase + (uint32_t)oi * kPBBytes, G, P.err))
+        failed = true;
     }
     group_sync(g);
     if (failed) break;
@@ -342,7 +351,18 @@ sv_status launch_tile_tcp(sv_state *s, const TilePass &p, const HostPass &host, 
   const uint64_t ntiles = 1ull << (p.n - p.m);
   const uint64_t per_cta = (uint64_t)kPGroups;
   const int grid = (int)std::min<uint64_t>((ntiles + per_cta - 1) / per_cta, (uint64_t)s->sm_count);
-  k_tile_tcp<<<grid, kPThreads, tcp_smem_bytes(p.nops), stream>>>(p);
+  TcpTable tab;
+  std::memset(&tab, 0, sizeof(tab));
+  for (int i = 0; i < p.nops; i++) {
+    const TileOp &op = host.ops[i];
+    for (int y = 0; y < 32; y++) {
+      uint32_t l = 0;
+      for (int j = 0; j < 5; j++) l |= (uint32_t)((y >> j) & 1) << op.t[j];
+      tab.soff[i][y] = tcp_swz(l);
+    }
+    for (int b = 0; b < 7; b++) tab.rbit[i][b] = tcp_swz(1u << ((op.tbpos[b >> 1] >> (4 * (b & 1))) & 15u));
+  }
+  k_tile_tcp<<<grid, kPThreads, tcp_smem_bytes(p.nops), stream>>>(p, tab);
   g_launches++;
   SV_CUDA(cudaGetLastError());
   return SV_OK;

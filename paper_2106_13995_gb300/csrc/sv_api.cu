@@ -749,6 +749,11 @@ sv_status sv_plan_fmas(sv_state *s, const sv_circuit *c, const double *params, c
   SV_TRY(get_program(s, c, params, opt, &cp, &o));
   double f = 0;
   for (const Block &b : cp->blocks) {
+    // split-BF16 tile passes run every tensor-core block as a 5-qubit block
+    if (b.kind == TOP_TC) {
+      f += 4.0 * 32.0;
+      continue;
+    }
     if (b.kind != TOP_DENSE) continue;
     const double share = std::ldexp(1.0, -(int)b.controls.size());
     f += b.diag ? 4.0 * share : 4.0 * std::ldexp(1.0, (int)b.qubits.size()) * share;
