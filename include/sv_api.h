@@ -151,8 +151,22 @@ sv_status sv_create(int n_qubits, sv_dtype dtype, void *amps_dev, size_t amps_by
                     void *ws_dev, size_t ws_bytes, void *stream, sv_state **out);
 sv_status sv_destroy(sv_state *s);
 
-/* psi := |index>  (one write pass).  SV_EINVAL if index >= 2^n. */
+/* psi := |index>  (one write pass).  SV_EINVAL if index >= 2^n.
+ * The handle then knows the state is a basis state: sv_apply_circuit
+ * follows it through circuits whose every gate maps a basis state to a
+ * basis state times a phase (X, CNOT, Toffoli and other multi-controlled X,
+ * SWAP, Z, S, T, CZ, fSim(pi/2, phi), diagonal and monomial matrices, any
+ * controls) on the host and rewrites two amplitudes, with no pass over the
+ * state -- the reversible-arithmetic case of the paper's multiplier circuits
+ * (Sec. III-A) and the sparsity remark of Sec. IV.  Every other library
+ * call that writes the amplitudes ends this; a caller that writes the
+ * amplitude buffer itself must call sv_mark_modified (or sv_set_basis /
+ * sv_upload) before the next sv_apply_circuit. */
 sv_status sv_set_basis(sv_state *s, uint64_t index);
+/* Declare that the caller changed the amplitudes outside the library (for
+ * example through the tensor that owns them): the handle forgets that the
+ * state was a basis state.  Never fails for a valid handle. */
+sv_status sv_mark_modified(sv_state *s);
 /* Copy 2^n amplitudes host -> device / device -> host (bytes must equal the
  * state size); synchronous w.r.t. the host.  Used for checkpoints and for
  * end-to-end runs that start from a host state. */
@@ -182,6 +196,10 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
  * passes so that each pass reads and writes the state once.
  *   params: host FP64 vector of c->n_params (may be NULL if none is used).
  *   opt:    may be NULL (defaults).
+ * Fused blocks whose matrix is a 0/1 permutation (CNOT, Toffoli, C^3X and
+ * their products) only move amplitudes inside the tile; a state known to be
+ * a basis state (see sv_set_basis) takes no pass at all when every gate
+ * maps basis states to basis states.
  * Errors: SV_EINVAL (malformed op, width mismatch), SV_ENOMEM (program does
  * not fit the workspace). */
 sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params,

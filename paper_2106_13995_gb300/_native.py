@@ -75,6 +75,7 @@ def lib():
             "sv_create": (st, [C.c_int, C.c_int, vp, sz, vp, sz, vp, C.POINTER(vp)]),
             "sv_destroy": (st, [vp]),
             "sv_set_basis": (st, [vp, C.c_uint64]),
+            "sv_mark_modified": (st, [vp]),
             "sv_upload": (st, [vp, vp, sz]),
             "sv_download": (st, [vp, vp, sz]),
             "sv_synchronize": (st, [vp]),

@@ -166,4 +166,30 @@ sv_status circuit_to_gates(const sv_circuit *c, const double *params, int n,
   return SV_OK;
 }
 
+bool propagate_basis(const std::vector<Gate> &gates, uint64_t &index, cd &amp) {
+  for (const Gate &g : gates) {
+    if (g.grad_gen > 0) return false;
+    bool on = true;
+    for (int q : g.controls) on = on && ((index >> q) & 1ull);
+    if (!on) continue;
+    const int k = (int)g.targets.size(), d = 1 << k;
+    int c = 0;
+    for (int j = 0; j < k; j++) c |= (int)((index >> g.targets[j]) & 1ull) << j;
+    // column c of U must hold exactly one nonzero entry
+    int r1 = -1;
+    for (int r = 0; r < d; r++)
+      if (g.U[(size_t)r * d + c] != cd(0.0)) {
+        if (r1 >= 0) return false;
+        r1 = r;
+      }
+    if (r1 < 0) return false;
+    amp *= g.U[(size_t)r1 * d + c];
+    for (int j = 0; j < k; j++) {
+      const uint64_t bit = 1ull << g.targets[j];
+      index = ((r1 >> j) & 1) ? (index | bit) : (index & ~bit);
+    }
+  }
+  return true;
+}
+
 }  // namespace sv

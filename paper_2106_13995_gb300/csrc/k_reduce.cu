@@ -66,6 +66,22 @@ sv_status launch_set_basis(sv_state *s, uint64_t index) {
   return SV_OK;
 }
 
+template <typename R>
+__global__ void k_move_basis(typename Cx<R>::T *a, uint64_t from, uint64_t to, R re, R im) {
+  if (from != to) a[from] = czero<typename Cx<R>::T>();
+  a[to] = cmake(re, im);
+}
+
+sv_status launch_move_basis(sv_state *s, uint64_t from, uint64_t to, cd amp) {
+  if (s->dt == SV_C64)
+    k_move_basis<float><<<1, 1, 0, s->stream>>>((float2 *)s->amps, from, to, (float)amp.real(), (float)amp.imag());
+  else
+    k_move_basis<double><<<1, 1, 0, s->stream>>>((double2 *)s->amps, from, to, amp.real(), amp.imag());
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
 sv_status launch_scale(sv_state *s, double f) {
   const uint64_t na = 1ull << s->n;
   const int g = red_grid(s, na);

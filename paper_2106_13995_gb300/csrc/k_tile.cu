@@ -139,6 +139,13 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
         if (op.vmask & 2) apply_op<R, INL>(v1, P.m, op, P.ops + oi, U, threadIdx.x, blockDim.x);
         break;
       }
+      case TOP_PERM: {
+        if ((base & gcm) != gcm) break;
+        const uint8_t *perm = static_cast<const uint8_t *>(P.mats) + (size_t)op.mat * sizeof(C);
+        if (op.vmask & 1) perm_op<R>(v0, P.m, P.ops + oi, op.k, perm, threadIdx.x, blockDim.x);
+        if (op.vmask & 2) perm_op<R>(v1, P.m, P.ops + oi, op.k, perm, threadIdx.x, blockDim.x);
+        break;
+      }
       case TOP_GRAD:
         grad_op<R>(v0, v1, P.m, op, acc);
         break;

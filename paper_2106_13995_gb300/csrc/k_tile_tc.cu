@@ -336,7 +336,13 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks) k_tile_tc(const __gr
         j++;
       } else {
         const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);
-        if ((base & gcm) == gcm) apply_op<float, false, true>(tile, P.m, op, P.ops + oi, mats + op.mat, threadIdx.x, blockDim.x);
+        if ((base & gcm) != gcm) {
+        } else if (op.kind == TOP_PERM) {
+          perm_op<float>(tile, P.m, P.ops + oi, op.k, reinterpret_cast<const uint8_t *>(mats + op.mat), threadIdx.x,
+                         blockDim.x);
+        } else {
+          apply_op<float, false, true>(tile, P.m, op, P.ops + oi, mats + op.mat, threadIdx.x, blockDim.x);
+        }
       }
     }
     __syncthreads();

@@ -179,6 +179,7 @@ static sv_status adjoint_batch(sv_state *const *psi, sv_state *const *lam, int B
   if (!s) return set_error(SV_EINVAL, "null state");
   SV_TRY(check_batch(psi, B, s->n, s->dt, s->stream));
   SV_TRY(check_batch(lam, B, s->n, s->dt, s->stream));
+  for (int b = 0; b < B; b++) psi[b]->basis_known = lam[b]->basis_known = false;
   if (nt < 0 || (nt > 0 && !terms)) return set_error(SV_EINVAL, "bad term list");
   const uint64_t lim = (1ull << s->n) - 1;
   for (int t = 0; t < nt; t++)

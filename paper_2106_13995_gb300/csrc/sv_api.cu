@@ -170,6 +170,26 @@ static void set_thread_positions(TileOp &op, uint32_t fixed, int m, sv_dtype dt)
   for (int i = 0; i < nf; i++) op.tbpos[i >> 1] |= (uint8_t)(P[i] << (4 * (i & 1)));
 }
 
+// perm[c] = the row of the single entry 1 in column c, if U (2^k x 2^k) is a
+// permutation matrix with exact 0/1 entries
+bool permutation_of(const std::vector<cd> &U, int k, int *perm) {
+  const int d = 1 << k;
+  uint32_t rows = 0;
+  for (int c = 0; c < d; c++) {
+    int r1 = -1;
+    for (int r = 0; r < d; r++) {
+      const cd u = U[(size_t)r * d + c];
+      if (u == cd(0.0)) continue;
+      if (u != cd(1.0) || r1 >= 0) return false;
+      r1 = r;
+    }
+    if (r1 < 0 || ((rows >> r1) & 1u)) return false;
+    rows |= 1u << r1;
+    perm[c] = r1;
+  }
+  return true;
+}
+
 void put_pairs_c64(std::vector<uint8_t> &pool, const cd *U, int k) {
   const int d = 1 << k;
   for (int p = 0; p < d / 2; p++)
@@ -216,7 +236,20 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
       else gcm |= 1ull << q;
     }
     if (blk.kind == TOP_DENSE && blk.diag) op.kind = TOP_DIAG;
-    if (op.kind == TOP_DENSE || op.kind == TOP_DIAG) {
+    // 0/1 permutation blocks of complex128 states move amplitudes instead of
+    // multiplying by 0 and 1 at the GB300's low FP64 rate (complex64 dense
+    // blocks are exact for such matrices and as fast)
+    int perm[8];
+    if (op.kind == TOP_DENSE && b.dt == SV_C128 && blk.inst < 0 && op.k <= 3 && permutation_of(blk.U, op.k, perm))
+      op.kind = TOP_PERM;
+    if (op.kind == TOP_PERM) {
+      uint32_t fixed = op.lcmask;
+      for (int j = 0; j < op.k; j++) fixed |= 1u << op.t[j];
+      set_thread_positions(op, fixed, tp.m, b.dt);
+      while (prog.mats.size() % 16) prog.mats.push_back(0);
+      op.mat = (uint32_t)(prog.mats.size() / ab);
+      for (int y = 0; y < (1 << op.k); y++) prog.mats.push_back((uint8_t)perm[y]);
+    } else if (op.kind == TOP_DENSE || op.kind == TOP_DIAG) {
       uint32_t fixed = op.lcmask;
       if (op.kind == TOP_DENSE)
         for (int j = 0; j < op.k; j++) fixed |= 1u << op.t[j];
@@ -650,12 +683,24 @@ sv_status sv_destroy(sv_state *s) {
 sv_status sv_set_basis(sv_state *s, uint64_t index) {
   if (!s) return set_error(SV_EINVAL, "null state");
   if (index >= (1ull << s->n)) return set_error(SV_EINVAL, "basis index out of range");
-  return launch_set_basis(s, index);
+  s->basis_known = false;
+  SV_TRY(launch_set_basis(s, index));
+  s->basis_known = true;
+  s->basis_index = index;
+  s->basis_amp = 1.0;
+  return SV_OK;
+}
+
+sv_status sv_mark_modified(sv_state *s) {
+  if (!s) return set_error(SV_EINVAL, "null state");
+  s->basis_known = false;
+  return SV_OK;
 }
 
 sv_status sv_upload(sv_state *s, const void *host, size_t bytes) {
   if (!s || !host) return set_error(SV_EINVAL, "null argument");
   if (bytes != ((size_t)1 << s->n) * amp_bytes(s->dt)) return set_error(SV_EINVAL, "size mismatch");
+  s->basis_known = false;
   SV_CUDA(cudaMemcpyAsync(s->amps, host, bytes, cudaMemcpyHostToDevice, s->stream));
   SV_CUDA(cudaStreamSynchronize(s->stream));
   return SV_OK;
@@ -690,6 +735,7 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
                         const double *matrix, int adjoint) {
   if (!s || !targets || !matrix) return set_error(SV_EINVAL, "null argument");
   if (k < 1 || k > 6) return set_error(SV_EINVAL, "k must be in [1, 6]");
+  s->basis_known = false;
   if (nctrl < 0 || nctrl > 8 || (nctrl > 0 && !controls)) return set_error(SV_EINVAL, "bad controls");
   uint64_t seen = 0;
   std::vector<int> t(k), c(nctrl);
@@ -721,9 +767,25 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
 
 
 sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const double *params, const sv_options *opt) {
+  if (s && c && s->basis_known) {
+    // a basis state through permutation and phase gates stays a basis
+    // state: follow it on the host and rewrite two amplitudes, with no pass
+    // over the state (exact: only the FP64 phases are rounded, once)
+    std::vector<Gate> gates;
+    SV_TRY(circuit_to_gates(c, params, s->n, gates, false));
+    uint64_t idx = s->basis_index;
+    cd amp = s->basis_amp;
+    if (propagate_basis(gates, idx, amp)) {
+      SV_TRY(launch_move_basis(s, s->basis_index, idx, amp));
+      s->basis_index = idx;
+      s->basis_amp = amp;
+      return SV_OK;
+    }
+  }
   ProgramRef cp;
   Opts o;
   SV_TRY(get_program(s, c, params, opt, &cp, &o));
+  s->basis_known = false;
   if (o.mode == SV_MODE_PER_GATE) return run_blocks_per_gate(s, cp->blocks);
   SV_TRY(upload_program(s, *cp));
   LaunchEnv E;

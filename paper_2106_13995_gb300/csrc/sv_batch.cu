@@ -294,6 +294,7 @@ sv_status sv_apply_circuit_batch(sv_state *const *states, int B, const sv_circui
     for (int b = 0; b < B; b++) SV_TRY(sv_apply_circuit(states[b], circs[b], params ? params[b] : nullptr, opt));
     return SV_OK;
   }
+  for (int b = 0; b < B; b++) states[b]->basis_known = false;
   return run_batch(states, B, circs, params, opt);
 }
 
@@ -301,6 +302,7 @@ sv_status sv_autotune(sv_state *s, const sv_circuit *c, sv_options *inout) {
   if (!s || !c || !inout) return set_error(SV_EINVAL, "null argument");
   if (c->n_qubits != s->n) return set_error(SV_EINVAL, "circuit width does not match the scratch state");
   if (c->n_params > 0) return set_error(SV_EUNSUPPORTED, "autotune a circuit with fixed angles");
+  s->basis_known = false;
   cudaEvent_t e0, e1;
   SV_CUDA(cudaEventCreate(&e0));
   SV_CUDA(cudaEventCreate(&e1));

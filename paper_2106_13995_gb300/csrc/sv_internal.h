@@ -51,7 +51,8 @@ enum TileOpKind : uint8_t {
   TOP_PAULI = 3,     // v1[l ^ xm] += c * phase * (-1)^{popcount(l & zm)} v0[l]
   TOP_ZERO = 4,      // v1 <- 0
   TOP_DOT = 5,       // acc[slot] += Re <v0 | v1>
-  TOP_TC = 6         // 5-qubit dense block on the tensor cores (12-qubit tiles)
+  TOP_TC = 6,        // 5-qubit dense block on the tensor cores (12-qubit tiles)
+  TOP_PERM = 7       // permutation block (k = 1..3): member y moves to member perm[y]; controls as TOP_DENSE
 };
 
 // 32-byte op descriptor; matrices live in a separate pool.
@@ -237,6 +238,12 @@ struct sv_state {
   cudaEvent_t staged = nullptr;     // last upload from `pinned` finished
   cudaStream_t capture = nullptr;   // library-owned stream used only to record CUDA graphs
   uint64_t resident = 0;            // serial of the program in the workspace program area (0: none)
+  // the state is known to be basis_amp |basis_index>: set by sv_set_basis,
+  // kept by circuits of permutation and phase gates, cleared by every other
+  // write to the amplitudes (and by sv_mark_modified)
+  bool basis_known = false;
+  uint64_t basis_index = 0;
+  std::complex<double> basis_amp = 1.0;
 };
 
 namespace sv {
@@ -402,6 +409,12 @@ void drop_adjoint_programs(const sv_state *s);
 
 // kernels (launchers), all enqueue on s->stream
 sv_status launch_set_basis(sv_state *s, uint64_t index);
+// psi[from] := 0, psi[to] := a (one thread; the state is a basis state)
+sv_status launch_move_basis(sv_state *s, uint64_t from, uint64_t to, cd a);
+// Follow a basis state through gates that map it to a basis state times a
+// phase (permutations, diagonal and monomial gates, with controls); false,
+// leaving index and amp unspecified, as soon as one gate does not.
+bool propagate_basis(const std::vector<Gate> &gates, uint64_t &index, cd &amp);
 sv_status launch_scale(sv_state *s, double factor);
 sv_status launch_dense_gate(sv_state *s, const std::vector<int> &targets,
                             const std::vector<int> &controls, const std::vector<cd> &U);
@@ -422,6 +435,8 @@ sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch);
 // in the row-pair layout the packed tile ops read: for p < 2^k / 2 and
 // column y, (Re U[2p][y], Re U[2p+1][y]) then (Im U[2p][y], Im U[2p+1][y]).
 void put_pairs_c64(std::vector<uint8_t> &pool, const cd *U, int k);
+// perm[c] = row of the single 1 in column c when U (2^k x 2^k, k <= 5) is a 0/1 permutation matrix
+bool permutation_of(const std::vector<cd> &U, int k, int *perm);
 // host copy of a pass's ops (the pass's first op) and of the program's matrix pool
 struct HostPass {
   const TileOp *ops;

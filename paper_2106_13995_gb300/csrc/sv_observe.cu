@@ -106,6 +106,7 @@ sv_status sv_renormalize(sv_state *s, double *out) {
   SV_TRY(sv_norm(s, &nrm));
   if (out) *out = nrm;
   if (!(nrm > 0) || !std::isfinite(nrm)) return set_error(SV_EINVAL, "state has zero or non-finite norm");
+  s->basis_known = false;
   return launch_scale(s, 1.0 / std::sqrt(nrm));
 }
 

@@ -454,6 +454,62 @@ __device__ __forceinline__ void apply_op(typename Cx<R>::T *v, int m, const Tile
   }
 }
 
+// Permutation block: a dense block whose matrix has one entry 1 in every
+// row and column (X, CNOT, Toffoli, C^3X and their products) only moves
+// amplitudes: member y of each control-satisfied group goes to member
+// perm[y] (perm: 2^K bytes).  No arithmetic, so the result is exact.  Out of
+// line, like the large dense blocks, so its registers stay off the hot path;
+// the op is read from global memory.
+template <typename R, int K>
+__device__ __noinline__ void perm_op_k(typename Cx<R>::T *__restrict__ v, int m, const TileOp *gop,
+                                       const uint8_t *__restrict__ perm, uint32_t tid, uint32_t T) {
+  using C = typename Cx<R>::T;
+  constexpr int D = 1 << K;
+  const TileOp op = *gop;
+  const uint32_t vs = smem_u32(v);
+  uint32_t soff[D], dst[D], tmask = 0;
+  soff[0] = 0;
+#pragma unroll
+  for (int j = 0; j < K; j++) {
+    const uint32_t bit = 1u << op.t[j];
+    tmask |= bit;
+    const uint32_t e = swb<R>(bit);
+#pragma unroll
+    for (int y = 0; y < (1 << j); y++) soff[y + (1 << j)] = soff[y] ^ e;
+  }
+#pragma unroll
+  for (int y = 0; y < D; y++) {
+    const uint32_t r = __ldg(perm + y) & (D - 1);
+    uint32_t so = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++) so ^= ((r >> j) & 1u) ? swb<R>(1u << op.t[j]) : 0u;
+    dst[y] = so;
+  }
+  const uint32_t fixed = tmask | op.lcmask;
+  const uint32_t ngroups = 1u << (m - __popc(fixed));
+  if (tid >= ngroups) return;
+  const uint32_t ntrips = ngroups > T ? ngroups / T : 1u;
+  const uint32_t sthr = swb<R>(thread_l(tid, op) | op.lcmask);
+  const TripMap tm = trip_map(T, fixed);
+  for (uint32_t c = 0; c < ntrips; c++) {
+    const uint32_t s = sthr ^ swb<R>(trip_l(c, tm));
+    C x[D];
+#pragma unroll
+    for (int y = 0; y < D; y++) x[y] = lds_c(vs + (s ^ soff[y]), (const C *)nullptr);
+#pragma unroll
+    for (int y = 0; y < D; y++) sts_c(vs + (s ^ dst[y]), x[y]);
+  }
+}
+template <typename R>
+__device__ __forceinline__ void perm_op(typename Cx<R>::T *v, int m, const TileOp *gop, int k, const uint8_t *perm,
+                                        uint32_t tid, uint32_t T) {
+  switch (k) {
+    case 1: perm_op_k<R, 1>(v, m, gop, perm, tid, T); break;
+    case 2: perm_op_k<R, 2>(v, m, gop, perm, tid, T); break;
+    default: perm_op_k<R, 3>(v, m, gop, perm, tid, T); break;
+  }
+}
+
 // Im(conj(b) a)
 template <typename C> __device__ __forceinline__ auto imdot(C b, C a) -> decltype(a.x) {
   return b.x * a.y - b.y * a.x;

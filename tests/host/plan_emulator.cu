@@ -98,7 +98,14 @@ extern "C" int plan_emulate(const sv_circuit *c, double *psi_, int fusion_k, int
             for (int j = 0; j < K; j++) r |= ((l >> op.t[j]) & 1u) << j;
             v[l] = U[r] * v[l];
           }
-        } else if (op.kind == TOP_DENSE) {
+        } else if (op.kind == TOP_DENSE || op.kind == TOP_PERM) {
+          std::vector<cx> Up;
+          if (op.kind == TOP_PERM) {   // table perm[c] = row of column c's 1
+            const uint8_t *perm = prog.mats.data() + (size_t)op.mat * sizeof(cx);
+            Up.assign((size_t)D * D, 0.0);
+            for (int q = 0; q < D; q++) Up[(size_t)perm[q] * D + q] = 1.0;
+            U = Up.data();
+          }
           std::vector<uint32_t> off(D);
           for (int y = 0; y < D; y++) {
             uint32_t o = 0;
@@ -153,9 +160,9 @@ extern "C" int check_thread_positions(const sv_circuit *c, int fusion_k, int m, 
     const TilePass &tp = prog.passes[pi];
     for (int oi = 0; oi < tp.nops; oi++) {
       const TileOp &op = prog.ops[op0s[pi] + oi];
-      if (op.kind != TOP_DENSE && op.kind != TOP_DIAG) continue;
+      if (op.kind != TOP_DENSE && op.kind != TOP_DIAG && op.kind != TOP_PERM) continue;
       uint32_t fixed = op.lcmask;
-      if (op.kind == TOP_DENSE)
+      if (op.kind == TOP_DENSE || op.kind == TOP_PERM)
         for (int j = 0; j < op.k; j++) fixed |= 1u << op.t[j];
       const uint32_t ngroups = 1u << (tp.m - __builtin_popcount(fixed));
       auto thread_l = [&](uint32_t t) {
@@ -375,6 +382,9 @@ extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure)
             const double im = (double)bf16_at(hi, 2 * r + 1, 2 * q) + (double)bf16_at(lo, 2 * r + 1, 2 * q);
             U[(size_t)r * 32 + q] = cx(re, im);
           }
+      } else if (op.kind == TOP_PERM) {
+        U.assign((size_t)D * D, 0.0);
+        for (int q = 0; q < D; q++) U[(size_t)base[q] * D + q] = 1.0;
       } else if (op.kind == TOP_DIAG) {
         const float *f = reinterpret_cast<const float *>(base);
         U.resize(D);
@@ -445,4 +455,19 @@ extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure)
     }
   }
   return (int)prog.passes.size();
+}
+
+// The library's basis-state propagation (sv_apply_circuit's fast path) on
+// the host: follows |index> through the circuit's gates.  Returns 1 and the
+// final index and amplitude, or 0 when some gate does not keep a basis
+// state a basis state.
+extern "C" int basis_propagate(const sv_circuit *c, uint64_t index, uint64_t *out_index, double *amp_re_im) {
+  std::vector<Gate> gates;
+  if (circuit_to_gates(c, nullptr, c->n_qubits, gates, false) != SV_OK) return -1;
+  cd amp = 1.0;
+  if (!propagate_basis(gates, index, amp)) return 0;
+  *out_index = index;
+  amp_re_im[0] = amp.real();
+  amp_re_im[1] = amp.imag();
+  return 1;
 }

@@ -49,6 +49,11 @@ def test_mixed_random_all_fusions_and_tiles(svlib, oracle, dt, fk, m):
     inf, amp = fidelity_metrics(want, s.numpy())
     tol = 1e-5 if dt == "c64" else 1e-12
     assert inf <= tol, (inf, amp)
+    # per amplitude: a few units of the state's rounding, relative to the
+    # largest amplitude (complex64 ~6e-8 per operation, complex128 ~1e-16)
+    amp_tol = (1e-5 if dt == "c64" else 1e-13) * float(np.max(np.abs(want)))
+    assert amp <= amp_tol, (amp, amp_tol)
+    print(f"{dt} fk={fk} m={m}: 1-F {inf:.2e}, max |d psi| {amp:.2e}")
 
 
 @pytest.mark.parametrize("nops", [47, 48, 49, 200])
@@ -116,15 +121,24 @@ def test_grid_4x4(svlib, oracle):
         assert inf <= 1e-5, (opts, inf)
 
 
-def test_grid_26q_instance(svlib, oracle):
-    """The 26-qubit width-reduced 5x6 grid circuit, complex64 vs FP64 oracle."""
+@pytest.mark.parametrize("prec", ["plain", "bf16x3"])
+def test_grid_26q_instance(svlib, oracle, prec):
+    """The 26-qubit width-reduced 5x6 grid circuit, complex64 vs FP64 oracle,
+    with FP32 CUDA-core blocks and with split-BF16 tensor-core blocks (the
+    bench's arithmetic)."""
+    from paper_2106_13995_gb300 import _native as N
     c = W.remove_qubits(W.grid_random(5, 6, 20, seed=1), 4, seed=101)
     want = oracle.run(c)
-    s = run_gpu(svlib, c, "c64")
+    opts = svlib.options(prec=N.SV_PREC_TC_BF16X3 if prec == "bf16x3" else N.SV_PREC_PLAIN)
+    s = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c, opts=opts)
     got = s.numpy()
     inf, amp = fidelity_metrics(want, got)
+    rms = float(np.sqrt(np.mean(np.abs(want) ** 2)))
     assert inf <= 1e-5, inf
-    print(f"grid 26q c64: 1-F = {inf:.3e}, max |d psi| = {amp:.3e}")
+    # per amplitude within 1e-3 of the rms amplitude (the error of one block is
+    # ~1e-7 (FP32) or ~1e-5 (split-BF16) of the amplitudes it mixes)
+    assert amp <= 1e-3 * rms, (amp, rms)
+    print(f"grid 26q c64 {prec}: 1-F = {inf:.3e}, max |d psi| = {amp:.3e} (rms amplitude {rms:.3e})")
 
 
 def test_ghz_and_qft(svlib, oracle):
@@ -151,6 +165,27 @@ def test_multiplier_3bit_all_inputs(svlib):
             v = s.numpy()
             idx = W.multiplier_basis_index(a, b, nb, a * b)
             assert v[idx] == 1 and np.count_nonzero(v) == 1
+
+
+def test_multiplier_complex128_permutation_ops(svlib, oracle):
+    """complex128 tile passes apply the multiplier's blocks as permutation
+    ops (no FP64 arithmetic): every basis input of the 3-bit multiplier,
+    through the tile passes (the basis-state path switched off), and the
+    superposed 5-bit multiplier against the oracle, exactly."""
+    from paper_2106_13995_gb300 import _native as N
+    nb = 3
+    c = W.multiplier(nb)
+    s = svlib.StateVector(c.n_qubits, "c128")
+    for a in range(8):
+        for b in range(8):
+            s.set_basis(W.multiplier_basis_index(a, b, nb))
+            N.check(N.lib().sv_mark_modified(s.h))
+            v = s.apply_circuit(c).numpy()
+            idx = W.multiplier_basis_index(a, b, nb, a * b)
+            assert v[idx] == 1 and np.count_nonzero(v) == 1
+    c5 = W.multiplier(5, hadamard_inputs=True)
+    got = svlib.StateVector(c5.n_qubits, "c128").set_basis(0).apply_circuit(c5).numpy()
+    assert np.max(np.abs(got - oracle.run(c5))) <= 1e-15
 
 
 def test_multiplier_29q_basis_inputs(svlib):
@@ -194,6 +229,57 @@ def test_multiplier_superposed_inputs(svlib):
         a, b = x & 127, (x >> 7) & 127
         assert x == W.multiplier_basis_index(a, b, nb, a * b)
     assert abs(s.norm2() - 1) <= 1e-6
+
+
+def test_multiplier_basis_fast_path_equals_dense_path(svlib):
+    """A state set by sv_set_basis goes through the 29-qubit multiplier as a
+    host-side index update (two amplitudes rewritten); after
+    sv_mark_modified the same input takes the tile passes, whose blocks are
+    permutation ops.  Both give the same bits, and the fast path launches a
+    single one-thread kernel."""
+    import torch
+    from paper_2106_13995_gb300 import _native as N
+    nb = 7
+    m = svlib.marshal(W.multiplier(nb))
+    fast = svlib.StateVector(4 * nb + 1, "c64")
+    dense = svlib.StateVector(4 * nb + 1, "c64")
+    rng = np.random.default_rng(12)
+    for a, b in rng.integers(0, 128, size=(4, 2)):
+        idx = W.multiplier_basis_index(int(a), int(b), nb)
+        fast.set_basis(idx)
+        l0 = svlib.kernel_launches()
+        fast.apply_circuit(m)
+        assert svlib.kernel_launches() - l0 == 1
+        dense.set_basis(idx)
+        N.check(N.lib().sv_mark_modified(dense.h))
+        dense.apply_circuit(m)
+        torch.cuda.synchronize()
+        assert torch.equal(fast.amps, dense.amps), (a, b)
+        want = W.multiplier_basis_index(int(a), int(b), nb, int(a) * int(b))
+        assert fast.amps[2 * want].item() == 1.0
+    # a non-permutation circuit ends the basis-state path
+    fast.set_basis(0)
+    fast.apply_circuit(W.Circuit(4 * nb + 1, [W.Op("H", (0,))]))
+    fast.apply_circuit(m)
+    v = fast.amps.view(-1, 2)
+    assert torch.count_nonzero(v[:, 0]).item() == 2
+
+
+def test_multiplier_29q_superposed_exhaustive(svlib):
+    """H on all 14 input qubits of the 29-qubit multiplier: checked on the
+    device over all 2^29 amplitudes -- exactly 2^14 nonzero, each at
+    |a, b, a*b, 0> with probability 2^-14 (within 1e-6 relative)."""
+    import torch
+    nb = 7
+    s = run_gpu(svlib, W.multiplier(nb, hadamard_inputs=True), "c64")
+    v = torch.view_as_complex(s.amps.view(-1, 2))
+    nz = torch.count_nonzero(v).item()
+    assert nz == 1 << (2 * nb)
+    ab = torch.arange(1 << (2 * nb), device=v.device, dtype=torch.int64)
+    a, b = ab & 127, ab >> 7
+    idx = a | (b << nb) | ((a * b) << (2 * nb))
+    p = (v[idx].abs().double() ** 2)
+    assert torch.max(torch.abs(p - 2.0 ** -14)).item() <= 1e-6 * 2.0 ** -14
 
 
 def test_program_cache_reuse_and_params(svlib, oracle):

@@ -170,3 +170,49 @@ def test_split_bf16_programs_match_oracle(emu, oracle):
         inf = oracle.infidelity(want, psi)
         assert inf <= 1e-8, (c.name, inf)
         assert np.max(np.abs(psi - want)) <= 1e-4 * np.max(np.abs(want)), c.name
+
+
+def test_basis_propagation_matches_oracle(emu, oracle):
+    """The host-side basis-state path: through the multiplier (X, CNOT,
+    Toffoli, C^3X) every basis input |a, b, 0, 0> goes to |a, b, a*b, 0> with
+    amplitude exactly 1; through permutation and phase gates (SWAP, CZ, S, T,
+    fSim(pi/2, phi), controlled X) the index and phase match the oracle's
+    single nonzero amplitude; a Hadamard stops the path."""
+    from paper_2106_13995_gb300 import sim
+    emu.basis_propagate.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64), C.c_void_p]
+    nb = 3
+    m = sim.marshal(W.multiplier(nb))
+    out = C.c_uint64()
+    amp = np.zeros(2)
+    for a in range(8):
+        for b in range(8):
+            assert emu.basis_propagate(C.addressof(m.c), W.multiplier_basis_index(a, b, nb), C.byref(out),
+                                       amp.ctypes.data) == 1
+            assert out.value == W.multiplier_basis_index(a, b, nb, a * b), (a, b)
+            assert amp[0] == 1.0 and amp[1] == 0.0
+    rng = np.random.default_rng(4)
+    n = 7
+    for trial in range(6):
+        c = W.Circuit(n)
+        for _ in range(30):
+            g = rng.choice(["SWAP", "CZ", "S", "T", "FSIM", "CX", "Y", "Z"])
+            q = [int(x) for x in rng.choice(n, size=3, replace=False)]
+            if g in ("SWAP", "CZ"):
+                c.ops.append(W.Op(g, (q[0], q[1])))
+            elif g == "FSIM":
+                c.ops.append(W.Op("FSIM", (q[0], q[1]), angles=(np.pi / 2, np.pi / 6)))
+            elif g == "CX":
+                c.ops.append(W.Op("X", (q[0],), controls=(q[1], q[2])))
+            else:
+                c.ops.append(W.Op(g, (q[0],)))
+        idx0 = int(rng.integers(0, 1 << n))
+        mm = sim.marshal(c)
+        assert emu.basis_propagate(C.addressof(mm.c), idx0, C.byref(out), amp.ctypes.data) == 1
+        psi0 = np.zeros(1 << n, complex)
+        psi0[idx0] = 1
+        want = oracle.run(c, psi0)
+        nz = np.flatnonzero(np.abs(want) > 1e-12)
+        assert list(nz) == [out.value]
+        assert abs(want[out.value] - complex(amp[0], amp[1])) <= 1e-13
+    h = W.Circuit(n, [W.Op("X", (0,)), W.Op("H", (1,))])
+    assert emu.basis_propagate(C.addressof(sim.marshal(h).c), 0, C.byref(out), amp.ctypes.data) == 0
