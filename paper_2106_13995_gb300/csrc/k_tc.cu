@@ -190,10 +190,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dense_tc(const __grid_constan
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// Host: real embedding R of U (64 x 64), split into hi/lo parts and laid out
-// as the K-major B operand (B[n][k] = R[n][k]).
+// Host: real embedding R of U (64 x 64 for 5 qubits, 128 x 128 for 6), split
+// into hi/lo parts and laid out as the K-major B operand (B[n][k] = R[n][k]).
 static void build_b(const std::vector<cd> &U, uint32_t mode, std::vector<uint32_t> &out) {
-  const int D = 32, N = 64;
+  const int D = U.size() == 64 * 64 ? 64 : 32, N = 2 * D;   // 5- or 6-qubit block
   std::vector<float> R((size_t)N * N);
   for (int r = 0; r < D; r++)
     for (int c = 0; c < D; c++) {
@@ -231,7 +231,10 @@ static void build_b(const std::vector<cd> &U, uint32_t mode, std::vector<uint32_
     }
 }
 
-size_t tc_matrix_words(sv_prec mode) { return mode == SV_PREC_TC_TF32X3 ? 2 * 64 * 64 : 64 * 64; }
+size_t tc_matrix_words(sv_prec mode, int k) {
+  const size_t N = (size_t)2 << k;
+  return mode == SV_PREC_TC_TF32X3 ? 2 * N * N : N * N;
+}
 
 void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t> &out) {
   build_b(U, mode == SV_PREC_TC_TF32X3 ? 1u : 2u, out);
@@ -260,6 +263,170 @@ sv_status launch_dense_tc(sv_state *s, void *amps, const int *targets, const uin
   const uint64_t ntiles = A.ngroups / kTcRows;
   const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)s->sm_count * 2);
   k_dense_tc<<<grid, kTcThreads, kSmTotal, stream>>>(A);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// K10: a fused 6-qubit dense block on the tensor cores (split-BF16).
+//
+// The block's real embedding is 128 x 128; a CTA takes 128 groups of 64
+// amplitudes (M = 128, N = K = 128), two threads per group: thread t gathers
+// amplitudes 32h .. 32h + 31 (h = t / 128) of group t % 128 from HBM, splits
+// them into BF16 hi/lo parts and writes them into the A operand in shared
+// memory (canonical K-major layout); one thread issues the 3 x 8 MMAs, and
+// while they run every thread loads its share of the next tile into
+// registers; the warps then read their TMEM lanes back (warps w and w + 4
+// share a lane quadrant, each reading its half of the columns) and scatter.
+// Shared memory: A hi/lo 64 KB + B hi/lo 64 KB, one CTA per SM.
+// ---------------------------------------------------------------------------
+constexpr int kTc6Threads = 256;
+constexpr uint32_t kTc6ABytes = 128 * 128 * 2;      // one BF16 part of A (32 KB)
+constexpr uint32_t kTc6BBytes = 128 * 128 * 2;      // one BF16 part of B
+constexpr uint32_t kTc6SmA = 0, kTc6SmB = 2 * kTc6ABytes, kTc6SmBar = kTc6SmB + 2 * kTc6BBytes;
+constexpr uint32_t kTc6Smem = kTc6SmBar + 16;
+
+struct Tc6Args {
+  float2 *amps;
+  uint64_t ngroups;          // 2^{n-6}
+  uint64_t tmask;            // target bits
+  uint64_t off[64];          // index offset of local basis state y
+  const uint32_t *bmat;      // device: B_hi then B_lo, 128 x 128 BF16 each, core-matrix layout
+  uint32_t *err;
+  uint32_t spin_limit;
+};
+
+__global__ void __launch_bounds__(kTc6Threads, 1) k_dense_tc6(const __grid_constant__ Tc6Args A) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t bar = sbase + kTc6SmBar;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kTc6SmBar + 8);
+  __shared__ uint32_t s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & 127, half = tid >> 7;
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.bmat);
+    uint4 *dst = reinterpret_cast<uint4 *>(sm + kTc6SmB);
+    for (uint32_t i = tid; i < 2 * kTc6BBytes / 16; i += kTc6Threads) dst[i] = src[i];
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = instr_desc(1u, 128, 128);   // BF16, M = 128, N = 128
+  uint32_t phase = 0;
+  const uint64_t ntiles = A.ngroups / 128;
+  uint64_t tile = blockIdx.x;
+  float2 x[32];
+  uint64_t base = 0;
+  if (tile < ntiles) {
+    base = ins0_mask64(tile * 128 + row, A.tmask);
+#pragma unroll
+    for (int y = 0; y < 32; y++) x[y] = __ldcs(A.amps + base + A.off[32 * half + y]);
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
+    // this thread's 32 amplitudes = K columns 64 half .. 64 half + 63 of its
+    // row = core-matrix chunks 8 half .. 8 half + 7 (8 BF16 = 4 amplitudes each)
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const float2 a = x[4 * c + e];
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(a.x, a.y);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(a.x - hf.x, a.y - hf.y);
+        hw[e] = *reinterpret_cast<const uint32_t *>(&hb);
+        lw[e] = *reinterpret_cast<const uint32_t *>(&lb);
+      }
+      const uint32_t o = cm_offset(row, 8 * half + c, 128);
+      *reinterpret_cast<uint4 *>(sm + kTc6SmA + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4 *>(sm + kTc6SmA + kTc6ABytes + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+      const uint32_t a_hi = sbase + kTc6SmA, a_lo = a_hi + kTc6ABytes;
+      const uint32_t b_hi = sbase + kTc6SmB, b_lo = b_hi + kTc6BBytes;
+      const uint32_t as[3] = {a_hi, a_hi, a_lo}, bs[3] = {b_hi, b_lo, b_hi};
+      for (int t = 0; t < 3; t++)
+        for (uint32_t k = 0; k < 8; k++)   // K = 16 per MMA: two core matrices of 128 x 16 bytes
+          mma_issue(tmem, smem_desc(as[t] + k * 2 * 2048, 2048, 128), smem_desc(bs[t] + k * 2 * 2048, 2048, 128),
+                    idesc, (t > 0 || k > 0) ? 1u : 0u, 2u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                   : "memory");
+    }
+    // the next tile's amplitudes while the MMAs run
+    const uint64_t cur_base = base;
+    const uint64_t next = tile + gridDim.x;
+    float2 xn[32];
+    if (next < ntiles) {
+      base = ins0_mask64(next * 128 + row, A.tmask);
+#pragma unroll
+      for (int y = 0; y < 32; y++) xn[y] = __ldcs(A.amps + base + A.off[32 * half + y]);
+    }
+    if (tid == 0) {
+      s_ok = mbar_wait(bar, phase, A.spin_limit) ? 1u : 0u;
+      if (!s_ok) {
+        atomicExch(A.err, 1u);
+        mbar_wait(bar, phase, A.spin_limit);   // a last bounded chance for the MMAs to drain
+      }
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    uint32_t r[64];
+    tmem_ld64(tmem + ((uint32_t)((warp & 3) * 32) << 16) + 64 * half, r);
+#pragma unroll
+    for (int y = 0; y < 32; y++)
+      __stcs(A.amps + cur_base + A.off[32 * half + y],
+             make_float2(__uint_as_float(r[2 * y]), __uint_as_float(r[2 * y + 1])));
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();   // TMEM and the A operand are free for the next tile
+#pragma unroll
+    for (int y = 0; y < 32; y++) x[y] = xn[y];
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128));
+}
+
+sv_status launch_dense_tc6(sv_state *s, void *amps, const int *targets, const uint32_t *bmat_dev,
+                           uint64_t spin_limit, cudaStream_t stream) {
+  if (s->dt != SV_C64) return set_error(SV_EUNSUPPORTED, "tensor-core blocks need a complex64 state");
+  if (s->n < 13) return set_error(SV_EUNSUPPORTED, "6-qubit tensor-core blocks need at least 13 qubits");
+  if (((uintptr_t)bmat_dev) & 15) return set_error(SV_EINVAL, "internal: tensor-core operand misaligned");
+  Tc6Args A;
+  std::memset(&A, 0, sizeof(A));
+  A.amps = reinterpret_cast<float2 *>(amps);
+  A.ngroups = 1ull << (s->n - 6);
+  for (int y = 0; y < 64; y++) {
+    uint64_t o = 0;
+    for (int j = 0; j < 6; j++) o |= (uint64_t)((y >> j) & 1) << targets[j];
+    A.off[y] = o;
+  }
+  A.tmask = A.off[63];
+  A.bmat = bmat_dev;
+  A.err = reinterpret_cast<uint32_t *>(s->ws + kWsCtrl + kWsErrFlag);
+  A.spin_limit = (uint32_t)std::min<uint64_t>(spin_limit ? spin_limit : (1u << 22), 0xFFFFFFFFu);
+  SV_TRY(func_attr_once((const void *)k_dense_tc6, s->device, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                        (int)kTc6Smem));
+  const uint64_t ntiles = A.ngroups / 128;
+  const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)s->sm_count);
+  k_dense_tc6<<<grid, kTc6Threads, kTc6Smem, stream>>>(A);
   g_launches++;
   SV_CUDA(cudaGetLastError());
   return SV_OK;

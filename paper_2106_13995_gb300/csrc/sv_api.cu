@@ -370,9 +370,10 @@ sv_status stage_upload(sv_state *s, const std::vector<std::pair<const void *, si
 
 sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream_t st, const HostPass *host) {
   if (!(tp.flags & kPassTC)) return launch_tile_pass_on(s, tp, batch, st, host);
-  int t[5];
-  for (int j = 0; j < 5; j++) t[j] = tp.hi_pos[j];
+  int t[6];
+  for (int j = 0; j < 6; j++) t[j] = tp.hi_pos[j];
   const uint32_t *b = reinterpret_cast<const uint32_t *>(static_cast<const char *>(tp.mats) + 16 * (size_t)tp.mat0);
+  if (tp.L == 6) return launch_dense_tc6(s, tp.v0, t, b, 0, st);
   return launch_dense_tc(s, tp.v0, t, b, (sv_prec)((tp.flags >> 9) & 3), 0, st);
 }
 
@@ -420,6 +421,27 @@ static void pad_in_tile(Block &blk, const std::vector<int> &S) {
       if ((r >> k) == (c >> k)) U5[(size_t)r * 32 + c] = blk.U[(size_t)(r & (d - 1)) * d + (c & (d - 1))];
   blk.U = std::move(U5);
   blk.diag = false;
+}
+
+// One dense block of 5 or 6 qubits as a tensor-core pass of its own.
+static sv_status emit_tc_pass(CachedProgram &out, const Block &blk, int n, int prec) {
+  TilePass tp;
+  std::memset(&tp, 0, sizeof(tp));
+  tp.n = n;
+  tp.m = n;
+  tp.L = (int)blk.qubits.size();
+  tp.nvec = 1;
+  tp.flags = kPassTC | ((uint32_t)prec << 9);
+  for (int j = 0; j < tp.L; j++) tp.hi_pos[j] = (int8_t)blk.qubits[j];
+  while (out.prog.mats.size() % 16) out.prog.mats.push_back(0);
+  tp.mat0 = (uint32_t)(out.prog.mats.size() / 16);
+  std::vector<uint32_t> packed;
+  tc_pack_matrix(blk.U, (sv_prec)prec, packed);
+  const uint8_t *pb = reinterpret_cast<const uint8_t *>(packed.data());
+  out.prog.mats.insert(out.prog.mats.end(), pb, pb + packed.size() * 4);
+  out.op0s.push_back((uint32_t)out.prog.ops.size());
+  out.prog.passes.push_back(tp);
+  return SV_OK;
 }
 
 static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gates, const Opts &o,
@@ -477,13 +499,32 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
       }
     }
     const int mat_cap = bf16 ? kTcpMaxBlocks * 1024 + 1023 : kMaxMatPerPass;
-    std::vector<PassPlan> passes = plan_passes(out.blocks, s->n, m, L, kMaxOpsPerPass, mat_cap);
-    if (passes.empty() && !out.blocks.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
-    for (PassPlan &P : passes) {
-      for (Block &blk : P.ops)
-        if (blk.kind == TOP_TC && blk.qubits.size() < 5) pad_in_tile(blk, P.S);
-      SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
+    std::vector<Block> seg;
+    auto flush_tc = [&]() -> sv_status {
+      if (seg.empty()) return SV_OK;
+      std::vector<PassPlan> passes = plan_passes(seg, s->n, m, L, kMaxOpsPerPass, mat_cap);
+      if (passes.empty()) return set_error(SV_EINVAL, "internal: pass planning failed");
+      for (PassPlan &P : passes) {
+        for (Block &blk : P.ops)
+          if (blk.kind == TOP_TC && blk.qubits.size() < 5) pad_in_tile(blk, P.S);
+        SV_TRY(emit_pass(out.prog, P, b, out.op0s, {}));
+      }
+      seg.clear();
+      return SV_OK;
+    };
+    for (const Block &blk : out.blocks) {
+      // split-BF16: an uncontrolled dense 6-qubit block (fusion width 6) is
+      // a tensor-core pass of its own, between the tile passes
+      const bool six = bf16 && s->n >= 13 && blk.kind == TOP_DENSE && blk.qubits.size() == 6 &&
+                       blk.controls.empty() && !blk.diag;
+      if (!six) {
+        seg.push_back(blk);
+        continue;
+      }
+      SV_TRY(flush_tc());
+      SV_TRY(emit_tc_pass(out, blk, s->n, o.prec));
     }
+    SV_TRY(flush_tc());
     out.lay = layout_of(out.prog, 0, 0);
     return SV_OK;
   }
@@ -505,21 +546,7 @@ static sv_status build_circuit_program(sv_state *s, const std::vector<Gate> &gat
       continue;
     }
     SV_TRY(flush());
-    TilePass tp;
-    std::memset(&tp, 0, sizeof(tp));
-    tp.n = s->n;
-    tp.m = s->n;
-    tp.nvec = 1;
-    tp.flags = kPassTC | ((uint32_t)o.prec << 9);
-    for (int j = 0; j < 5; j++) tp.hi_pos[j] = (int8_t)blk.qubits[j];
-    while (out.prog.mats.size() % 16) out.prog.mats.push_back(0);
-    tp.mat0 = (uint32_t)(out.prog.mats.size() / 16);
-    std::vector<uint32_t> packed;
-    tc_pack_matrix(blk.U, (sv_prec)o.prec, packed);
-    const uint8_t *pb = reinterpret_cast<const uint8_t *>(packed.data());
-    out.prog.mats.insert(out.prog.mats.end(), pb, pb + packed.size() * 4);
-    out.op0s.push_back((uint32_t)out.prog.ops.size());
-    out.prog.passes.push_back(tp);
+    SV_TRY(emit_tc_pass(out, blk, s->n, o.prec));
   }
   SV_TRY(flush());
   out.lay = layout_of(out.prog, 0, 0);

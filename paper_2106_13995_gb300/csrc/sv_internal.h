@@ -102,9 +102,10 @@ struct TileInline {
   OpPre pre[kInlOps];
   float2 mats[kInlMat];
 };
-// TilePass.flags: this entry is not a tile pass but one 5-qubit dense block on
-// the tensor cores; hi_pos[0..4] hold its targets, mat0 the 16-byte index of
-// its packed operand in the matrix pool, bits 9..10 the sv_prec mode.
+// TilePass.flags: this entry is not a tile pass but one dense block of L = 5
+// or 6 qubits on the tensor cores; hi_pos[0..L) hold its targets, mat0 the
+// 16-byte index of its packed operand in the matrix pool, bits 9..10 the
+// sv_prec mode (6-qubit blocks: split-BF16 only).
 constexpr uint32_t kPassTC = 0x100;
 // TilePass.flags: the pass contains TOP_TC ops (allocate TMEM); mode in bits 9..10
 constexpr uint32_t kPassHasTC = 0x8;
@@ -454,10 +455,13 @@ bool tcp_pass_ok(const TilePass &p, const HostPass &host);
 // plan-time row map of a TOP_TC op for the pipelined kernel's bank layout
 void tcp_row_positions(TileOp &op);
 // tensor-core 5-qubit block (k_tc.cu)
-size_t tc_matrix_words(sv_prec mode);
+size_t tc_matrix_words(sv_prec mode, int k);
 void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t> &out);
 sv_status launch_dense_tc(sv_state *s, void *amps, const int *targets, const uint32_t *bmat_dev, sv_prec mode,
                           uint64_t spin_limit, cudaStream_t stream);
+// a 6-qubit dense block on the tensor cores, split-BF16, a pass of its own (k_tc.cu)
+sv_status launch_dense_tc6(sv_state *s, void *amps, const int *targets, const uint32_t *bmat_dev,
+                           uint64_t spin_limit, cudaStream_t stream);
 // one pass of a program (tile pass or tensor-core block) on stream st
 sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream_t st,
                           const HostPass *host = nullptr);

@@ -332,12 +332,35 @@ static float bf16_at(const uint8_t *part, int n, int k) {
   std::memcpy(&f, &bits, 4);
   return f;
 }
-extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure) {
+static std::vector<std::complex<double>> unpack_embedding(const uint8_t *base, int k) {
+  // B hi then lo parts (BF16, N x N, N = 2^(k+1)); U[r][q] = R[2r][2q] + i R[2r+1][2q]
+  const int D = 1 << k, N = 2 * D;
+  auto at = [&](const uint8_t *part, int nn, int kk) {
+    const uint32_t o = (uint32_t)(kk / 8) * N * 16 + (uint32_t)(nn / 8) * 128 + (uint32_t)(nn % 8) * 16 +
+                       (uint32_t)(kk % 8) * 2;
+    uint16_t h;
+    std::memcpy(&h, part + o, 2);
+    const uint32_t bits = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &bits, 4);
+    return (double)f;
+  };
+  const uint8_t *hi = base, *lo = base + (size_t)N * N * 2;
+  std::vector<std::complex<double>> U((size_t)D * D);
+  for (int r = 0; r < D; r++)
+    for (int q = 0; q < D; q++)
+      U[(size_t)r * D + q] = std::complex<double>(at(hi, 2 * r, 2 * q) + at(lo, 2 * r, 2 * q),
+                                                  at(hi, 2 * r + 1, 2 * q) + at(lo, 2 * r + 1, 2 * q));
+  return U;
+}
+
+extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure, int fusion_k, int *nsix) {
   typedef std::complex<double> cx;
   sv_state st;
   st.n = c->n_qubits;
   st.dt = SV_C64;
-  sv_options opt{0, 0, SV_PREC_TC_BF16X3, SV_MODE_TILED, 0};
+  sv_options opt{fusion_k, 0, SV_PREC_TC_BF16X3, SV_MODE_TILED, 0};
+  *nsix = 0;
   ProgramRef cp;
   Opts o;
   if (get_program(&st, c, nullptr, &opt, &cp, &o) != SV_OK) {
@@ -350,9 +373,30 @@ extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure)
   *npure = 0;
   for (size_t pi = 0; pi < prog.passes.size(); pi++) {
     const TilePass &tp = prog.passes[pi];
-    if (tp.flags & kPassTC) {
-      std::printf("unexpected tensor-core pass of its own\n");
-      return -1;
+    if (tp.flags & kPassTC) {   // one block of tp.L qubits over the whole state
+      const int K = tp.L, D = 1 << K;
+      if (K != 6) { std::printf("unexpected %d-qubit tensor-core pass\n", K); return -1; }
+      (*nsix)++;
+      const std::vector<cx> U = unpack_embedding(prog.mats.data() + 16 * (size_t)tp.mat0, K);
+      uint64_t tmask = 0;
+      std::vector<uint64_t> off(D);
+      for (int y = 0; y < D; y++) {
+        uint64_t o = 0;
+        for (int j = 0; j < K; j++) o |= (uint64_t)((y >> j) & 1) << tp.hi_pos[j];
+        off[y] = o;
+      }
+      tmask = off[D - 1];
+      std::vector<cx> x(D);
+      for (uint64_t base = 0; base < (1ull << n); base++) {
+        if (base & tmask) continue;
+        for (int y = 0; y < D; y++) x[y] = psi[base + off[y]];
+        for (int r = 0; r < D; r++) {
+          cx a = 0;
+          for (int y = 0; y < D; y++) a += U[(size_t)r * D + y] * x[y];
+          psi[base + off[r]] = a;
+        }
+      }
+      continue;
     }
     const HostPass hp{prog.ops.data() + cp->op0s[pi], prog.mats.data()};
     *npure += tcp_pass_ok(tp, hp) ? 1 : 0;

@@ -78,3 +78,50 @@ def test_tc_rejected_for_complex128(svlib, oracle):
     s = svlib.StateVector(13, "c128").set_basis(0).apply_circuit(c, opts=svlib.options(prec=2))
     inf, _ = fidelity_metrics(oracle.run(c), s.numpy())
     assert inf <= 1e-12
+
+
+def six_block_circuit(n, targets, rng):
+    c = W.Circuit(n)
+    c.ops.append(W.Op("MATRIX", tuple(targets), matrix=W.random_unitary(6, rng)))
+    return c
+
+
+@pytest.mark.parametrize("targets", [(0, 1, 2, 3, 4, 5), (5, 4, 3, 2, 1, 0), (7, 2, 11, 0, 13, 9),
+                                     (13, 12, 11, 10, 9, 8), (1, 5, 9, 12, 3, 6)])
+def test_six_qubit_block(svlib, oracle, targets):
+    """A fused 6-qubit block on the tensor cores (split-BF16, a pass of its
+    own: (2^(n-6) x 128) x (128 x 128) real GEMM) against the oracle, at the
+    same per-amplitude budget as 5-qubit blocks."""
+    rng = np.random.default_rng(sum(targets) + 6)
+    n = 14
+    c = six_block_circuit(n, targets, rng)
+    psi0 = W.random_state(n, rng)
+    s = svlib.StateVector(n, "c64").load(psi0)
+    opts = svlib.options(prec=MODES["bf16x3"], fusion_k=6)
+    assert s.plan_info(c, opts=opts) == (1, 1)
+    l0 = svlib.kernel_launches()
+    s.apply_circuit(c, opts=opts)
+    assert svlib.kernel_launches() - l0 == 1
+    want = oracle.run(c, psi0.astype(np.complex64).astype(np.complex128))
+    inf, amp = fidelity_metrics(want, s.numpy())
+    assert amp <= AMP_TOL["bf16x3"] * np.max(np.abs(want)), amp
+    assert inf <= 1e-8
+
+
+def test_six_qubit_blocks_many_tiles_and_circuits(svlib, oracle):
+    rng = np.random.default_rng(66)
+    n = 20
+    c = six_block_circuit(n, (19, 3, 0, 10, 17, 7), rng)
+    psi0 = W.random_state(n, rng)
+    s = svlib.StateVector(n, "c64").load(psi0)
+    s.apply_circuit(c, opts=svlib.options(prec=MODES["bf16x3"], fusion_k=6))
+    want = oracle.run(c, psi0.astype(np.complex64).astype(np.complex128))
+    inf, amp = fidelity_metrics(want, s.numpy())
+    assert inf <= 1e-8 and amp <= AMP_TOL["bf16x3"] * np.max(np.abs(want))
+    # whole circuits at fusion width 6: 6-qubit passes between tile passes
+    for c in (W.random_u3_cz(16, 12, 3), W.grid_random(4, 4, 10, 2)):
+        opts = svlib.options(prec=MODES["bf16x3"], fusion_k=6)
+        st = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c, opts=opts)
+        inf, amp = fidelity_metrics(oracle.run(c), st.numpy())
+        assert inf <= 1e-5, (c.name, inf)
+        print(f"{c.name} bf16x3 k<=6: blocks/passes {st.plan_info(c, opts=opts)}, 1-F {inf:.2e}, max|d| {amp:.2e}")

@@ -154,15 +154,15 @@ def test_split_bf16_programs_match_oracle(emu, oracle):
     bits per entry); circuits without controlled gates take the pipelined
     kernel in every pass."""
     from paper_2106_13995_gb300 import sim
-    emu.tc_program_emulate.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+    emu.tc_program_emulate.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
     cases = [(W.grid_random(3, 5, 10, 1), True), (W.random_u3_cz(14, 8, 3), True),
              (W.remove_qubits(W.grid_random(5, 6, 6, 2), 16, 7), True), (W.multiplier(3), False)]
     for c, pure in cases:
         mm = sim.marshal(c)
         psi = np.zeros(1 << c.n_qubits, dtype=np.complex128)
         psi[0] = 1
-        npure = C.c_int()
-        npass = emu.tc_program_emulate(C.addressof(mm.c), psi.ctypes.data, C.byref(npure))
+        npure, nsix = C.c_int(), C.c_int()
+        npass = emu.tc_program_emulate(C.addressof(mm.c), psi.ctypes.data, C.byref(npure), 0, C.byref(nsix))
         assert npass > 0, c.name
         if pure:
             assert npure.value == npass, (c.name, npure.value, npass)
@@ -216,3 +216,22 @@ def test_basis_propagation_matches_oracle(emu, oracle):
         assert abs(want[out.value] - complex(amp[0], amp[1])) <= 1e-13
     h = W.Circuit(n, [W.Op("X", (0,)), W.Op("H", (1,))])
     assert emu.basis_propagate(C.addressof(sim.marshal(h).c), 0, C.byref(out), amp.ctypes.data) == 0
+
+
+def test_split_bf16_six_qubit_blocks(emu, oracle):
+    """Fusion width 6 in split-BF16: uncontrolled dense 6-qubit blocks become
+    tensor-core passes of their own (their 128 x 128 real embedding packed as
+    BF16 hi/lo parts), the rest stays in tile passes; unpacked and run on the
+    CPU the program reproduces the FP64 oracle to the split's precision."""
+    from paper_2106_13995_gb300 import sim
+    emu.tc_program_emulate.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
+    for c in (W.grid_random(3, 5, 10, 1), W.random_u3_cz(14, 10, 5)):
+        mm = sim.marshal(c)
+        psi = np.zeros(1 << c.n_qubits, dtype=np.complex128)
+        psi[0] = 1
+        npure, nsix = C.c_int(), C.c_int()
+        assert emu.tc_program_emulate(C.addressof(mm.c), psi.ctypes.data, C.byref(npure), 6, C.byref(nsix)) > 0
+        assert nsix.value > 0, c.name
+        want = oracle.run(c)
+        assert oracle.infidelity(want, psi) <= 1e-8, c.name
+        assert np.max(np.abs(psi - want)) <= 1e-4 * np.max(np.abs(want)), c.name
