@@ -3,9 +3,12 @@
 The state (2^n complex amplitudes) stays in GPU memory and gates are applied
 to it in place by hand-written sm_103a CUDA kernels behind a C ABI
 (``include/sv_api.h``, library ``_build/libsv.so``).  This package holds the
-build script and a thin ctypes binding.
+build script, a thin ctypes binding (``sim``), a circuit builder with Pauli
+observables and a simulator facade (``circuit``), and the multi-GPU sharding
+planner and executor (``shard``).
 """
 from . import _native  # noqa: F401
+from .circuit import Circuit, I, Parameter, PauliSum, Simulator, X, Y, Z, grid_qubit, ising  # noqa: F401
 
 
 def build(force: bool = False) -> str:
