@@ -608,10 +608,12 @@ def main():
         psis = [sim.StateVector(na, "c64", device=dev).set_basis(0) for _ in range(B)]
         lams = [sim.StateVector(na, "c64", device=dev) for _ in range(B)]
 
-        def batched():
+        gopt = sim.options(mode=NN.SV_MODE_TILED_GRAPH)
+
+        def batched():   # one replayed launch sequence per call
             for p in psis:
                 p.set_basis(0)
-            return sim.adjoint_grad_batch(psis, lams, hm, params, terms)
+            return sim.adjoint_grad_batch(psis, lams, hm, params, terms, opts=gopt)
 
         def plain():
             for b in range(B):
@@ -626,7 +628,9 @@ def main():
         tp = timed(plain, 1)
         out["adjoint"] = {"grads_per_s_batched": B / tb, "grads_per_s_plain": B / tp,
                           "speedup": tp / tb, "batch": B, "n_qubits": na, "gates": len(h.ops),
-                          "params": h.n_params, "state": "complex64, FP64 reductions"}
+                          "params": h.n_params, "state": "complex64, FP64 reductions",
+                          "batched_launch": "64 parameter sets per call; the accumulator reset and every pass "
+                                            "replayed from one CUDA graph (SV_MODE_TILED_GRAPH)"}
         del psis, lams
 
     # ---- uneven batch: 256 circuits of widths 10..24, one persistent launch -------
@@ -659,6 +663,28 @@ def main():
         tbu = timed(uneven_batched, ku) / ku
         N.check(N.lib().sv_synchronize(ust[0].h))
         tpu = timed(uneven_plain, ku) / ku
+        # the same batched call with split-BF16 tensor-core blocks: states of
+        # 12 or more qubits run the pipelined tensor-core tile passes inside
+        # the same recorded launch sequence, the smaller ones the persistent
+        # queue
+        gopt_tc = sim.options(mode=N.SV_MODE_TILED_GRAPH, prec=N.SV_PREC_TC_BF16X3)
+
+        def uneven_batched_tc():
+            for st_ in ust:
+                st_.set_basis(0)
+            N.check(N.lib().sv_apply_circuit_batch(hs, len(ust), cs, None, C.byref(gopt_tc)))
+
+        def uneven_plain_tc():
+            for st_, mm in zip(ust, ums):
+                st_.set_basis(0)
+                st_.apply_circuit(mm, opts=sim.options(prec=N.SV_PREC_TC_BF16X3))
+
+        uneven_batched_tc()
+        uneven_plain_tc()
+        N.check(N.lib().sv_synchronize(ust[0].h))
+        tbu_tc = timed(uneven_batched_tc, ku) / ku
+        N.check(N.lib().sv_synchronize(ust[0].h))
+        tpu_tc = timed(uneven_plain_tc, ku) / ku
         # fused 5-qubit blocks on the tensor cores (split-BF16 / split-TF32)
         # vs plain complex64 per-gate passes, same batch; accuracy of each
         # against the plain tiled complex64 result (the FP64-oracle errors
@@ -697,6 +723,9 @@ def main():
         per_mode["autotuned"]["choices"] = {str(k): [v.fusion_k, v.tile_m] for k, v in sorted(tuned.items())}
         out["uneven_batch"] = {"circuits_per_s_batched": len(circs) / tbu, "circuits_per_s_plain": len(circs) / tpu,
                                "speedup": tpu / tbu, "per_circuit_modes": per_mode,
+                               "bf16x3": {"circuits_per_s_batched": len(circs) / tbu_tc,
+                                          "circuits_per_s_per_circuit": len(circs) / tpu_tc,
+                                          "speedup": tpu_tc / tbu_tc},
                                "circuits": len(circs), "widths": "10..24", "depth": 40,
                                "gates": int(sum(len(c.ops) for c in circs)),
                                "launch": "one CUDA graph per call: a persistent cooperative launch for states "

@@ -149,6 +149,11 @@ __device__ __forceinline__ void tile_body(const TilePass &P, uint64_t tile, int 
       case TOP_GRAD:
         grad_op<R>(v0, v1, P.m, op, acc);
         break;
+      case TOP_GRADU: {
+        const C *U = ((op.gen & kGenBatchMat) ? pmats : mats) + op.mat;
+        grad_u_op<R>(v0, v1, P.m, op, U, acc);
+        break;
+      }
       case TOP_PAULI: {
         const uint32_t xm = (uint16_t)op.slot;
         const uint32_t zl = op.lcmask;

@@ -15,12 +15,14 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 
 #include "sv_internal.h"
 
 namespace sv {
 
 struct AdjointProgram {
+  uint64_t serial = 0;            // unique per built program (graph cache key)
   DeviceProgram prog;
   std::vector<uint32_t> op0s;
   std::vector<int> inst_param;   // parameter index of each parametric instance
@@ -30,7 +32,35 @@ struct AdjointProgram {
 };
 
 static ProgCache<AdjointProgram> g_adj_cache(64);
-void drop_adjoint_programs(const sv_state *s) { g_adj_cache.drop_owner(s); }
+
+// Recorded launch sequences of batched gradients (SV_MODE_TILED_GRAPH): the
+// accumulator reset and every pass, per (first state, program, batch layout).
+struct AdjGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+using AdjGraphKey = std::pair<const sv_state *, std::vector<uint64_t>>;
+static std::map<AdjGraphKey, AdjGraph> g_adj_graphs;
+static std::mutex g_adj_graphs_mu;
+constexpr size_t kMaxAdjGraphs = 32;
+
+static void destroy_graph(AdjGraph &g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+}
+
+void drop_adjoint_programs(const sv_state *s) {
+  g_adj_cache.drop_owner(s);
+  std::lock_guard<std::mutex> lk(g_adj_graphs_mu);
+  for (auto it = g_adj_graphs.begin(); it != g_adj_graphs.end();) {
+    if (it->first.first == s) {
+      destroy_graph(it->second);
+      it = g_adj_graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
 
 static void append_passes(DeviceProgram &prog, std::vector<uint32_t> &op0s, const std::vector<PassPlan> &passes,
                           const BuildCtx &b, const std::vector<int> &bmo, sv_status &st) {
@@ -185,7 +215,14 @@ static sv_status adjoint_batch(sv_state *const *psi, sv_state *const *lam, int B
   for (int t = 0; t < nt; t++)
     if ((terms[t].x_mask & ~lim) || (terms[t].z_mask & ~lim))
       return set_error(SV_EINVAL, "Pauli mask references a qubit >= n");
-  const Opts o1 = resolve(s, opt, 1), o2 = resolve(s, opt, 2);
+  Opts o1 = resolve(s, opt, 1), o2 = resolve(s, opt, 2);
+  // defaults for the gradient program (measured on the 20-qubit, 64-set
+  // ansatz): fusion width 2 and 12-qubit tiles for both sweeps
+  if (!opt || opt->fusion_k == 0) o1.fusion_k = o2.fusion_k = 2;
+  if (!opt || opt->tile_m == 0) {
+    o1.tile_m = o2.tile_m = std::min(12, s->n);
+    o1.L = o2.L = std::min(o1.L, o1.tile_m);
+  }
   // cache key: circuit structure, terms, options (parameters enter only the
   // per-batch matrices, uploaded every call)
   KeyBytes k;
@@ -200,6 +237,7 @@ static sv_status adjoint_batch(sv_state *const *psi, sv_state *const *lam, int B
   if (!Ap) {
     auto built = std::make_shared<AdjointProgram>();
     SV_TRY(build_adjoint(s, c, params, terms, nt, o1, o2, *built));
+    built->serial = next_program_serial();
     Ap = g_adj_cache.insert(s, k, kh, std::move(built));
   }
   const AdjointProgram &A = *Ap;
@@ -227,7 +265,6 @@ static sv_status adjoint_batch(sv_state *const *psi, sv_state *const *lam, int B
   const size_t acc_bytes = acc_stride * B * sizeof(double);
   if (acc_bytes > red_bytes(s->n)) return set_error(SV_ENOMEM, "workspace too small for the gradient batch");
   double *acc = reinterpret_cast<double *>(s->ws + kWsRed);
-  SV_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s->stream));
   char *base = s->ws + kWsProg;
   LaunchEnv E;
   E.batch = B;
@@ -237,7 +274,44 @@ static sv_status adjoint_batch(sv_state *const *psi, sv_state *const *lam, int B
   E.pmats_stride = (uint64_t)8 * A.n_inst;
   E.acc = acc;
   E.acc_stride = acc_stride;
-  SV_TRY(launch_program(s, A.prog, L, A.op0s, E));
+  if (opt && opt->mode == SV_MODE_TILED_GRAPH) {
+    // the reset and all passes as one recorded launch sequence; the tables
+    // and per-set matrices were uploaded above, in stream order, so a
+    // replay reads this call's parameters
+    std::lock_guard<std::mutex> lk(g_adj_graphs_mu);
+    AdjGraphKey gk{s, {Ap->serial, (uint64_t)B, (uint64_t)L.end, (uint64_t)acc_bytes}};
+    auto it = g_adj_graphs.find(gk);
+    if (it == g_adj_graphs.end()) {
+      AdjGraph g;
+      if (!s->capture) SV_CUDA(cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking));
+      SV_CUDA(cudaStreamBeginCapture(s->capture, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e1 = cudaMemsetAsync(acc, 0, acc_bytes, s->capture);
+      sv_status st = e1 == cudaSuccess ? launch_program(s, A.prog, L, A.op0s, E, s->capture)
+                                       : cuda_error(e1, "cudaMemsetAsync");
+      cudaError_t e2 = cudaStreamEndCapture(s->capture, &g.graph);
+      if (st != SV_OK) {
+        destroy_graph(g);
+        return st;
+      }
+      if (e2 != cudaSuccess) return cuda_error(e2, "cudaStreamEndCapture");
+      cudaError_t e3 = cudaGraphInstantiate(&g.exec, g.graph, 0);
+      if (e3 != cudaSuccess) {
+        destroy_graph(g);
+        return cuda_error(e3, "cudaGraphInstantiate");
+      }
+      if (g_adj_graphs.size() >= kMaxAdjGraphs) {
+        SV_CUDA(cudaStreamSynchronize(s->stream));   // replays in flight finish first
+        for (auto &kv : g_adj_graphs) destroy_graph(kv.second);
+        g_adj_graphs.clear();
+      }
+      it = g_adj_graphs.emplace(std::move(gk), g).first;
+    }
+    SV_CUDA(cudaGraphLaunch(it->second.exec, s->stream));
+    g_launches++;
+  } else {
+    SV_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s->stream));
+    SV_TRY(launch_program(s, A.prog, L, A.op0s, E));
+  }
   std::vector<double> h(acc_stride * B);
   SV_CUDA(cudaMemcpyAsync(h.data(), acc, acc_bytes, cudaMemcpyDeviceToHost, s->stream));
   SV_CUDA(cudaStreamSynchronize(s->stream));

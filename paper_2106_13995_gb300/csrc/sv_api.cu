@@ -220,7 +220,28 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
     if (loc[q] < 0) tp.out_pos[no++] = (int8_t)q;
   op0s.push_back((uint32_t)prog.ops.size());
   const size_t ab = amp_bytes(b.dt);
-  for (const Block &blk : P.ops) {
+  for (size_t bi = 0; bi < P.ops.size(); bi++) {
+    const Block &blk = P.ops[bi];
+    // the adjoint sweep's probe of a parametric gate directly followed by
+    // that gate's U^dagger on both vectors: one fused op
+    if (blk.kind == TOP_GRAD && bi + 1 < P.ops.size() && !batch_mat_off.empty()) {
+      const Block &u = P.ops[bi + 1];
+      if (u.kind == TOP_DENSE && u.inst >= 0 && u.qubits.size() == 1 && u.qubits == blk.qubits &&
+          u.controls.empty() && u.vmask == 3 && loc[blk.qubits[0]] >= 0) {
+        TileOp op;
+        std::memset(&op, 0, sizeof(op));
+        op.kind = TOP_GRADU;
+        op.k = 1;
+        op.vmask = 3;
+        op.t[0] = (uint8_t)loc[blk.qubits[0]];
+        op.gen = (uint8_t)(blk.gen | kGenBatchMat);
+        op.slot = (int16_t)blk.slot;
+        op.mat = (uint32_t)batch_mat_off[u.inst];
+        prog.ops.push_back(op);
+        bi++;
+        continue;
+      }
+    }
     TileOp op;
     std::memset(&op, 0, sizeof(op));
     op.kind = (uint8_t)blk.kind;
@@ -324,7 +345,7 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
     op.gcmask_hi = (uint16_t)(gcm >> 32);
     prog.ops.push_back(op);
   }
-  tp.nops = (int)P.ops.size();
+  tp.nops = (int)(prog.ops.size() - op0s.back());
   prog.passes.push_back(tp);
   return SV_OK;
 }
@@ -379,7 +400,8 @@ sv_status launch_any_pass(sv_state *s, const TilePass &tp, int batch, cudaStream
 
 // Launch every pass of a program.
 sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &L,
-                                const std::vector<uint32_t> &op0s, const LaunchEnv &E) {
+                                const std::vector<uint32_t> &op0s, const LaunchEnv &E, cudaStream_t st) {
+  if (!st) st = s->stream;
   char *base = s->ws + kWsProg;
   for (size_t i = 0; i < p.passes.size(); i++) {
     TilePass tp = p.passes[i];
@@ -396,7 +418,7 @@ sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &
     tp.v1 = E.v1;
     tp.err = reinterpret_cast<uint32_t *>(s->ws + kWsCtrl + kWsErrFlag);
     const HostPass hp{p.ops.data() + op0s[i], p.mats.data()};
-    SV_TRY(launch_any_pass(s, tp, E.batch, s->stream, &hp));
+    SV_TRY(launch_any_pass(s, tp, E.batch, st, &hp));
   }
   return SV_OK;
 }

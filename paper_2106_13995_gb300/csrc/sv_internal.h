@@ -52,7 +52,8 @@ enum TileOpKind : uint8_t {
   TOP_ZERO = 4,      // v1 <- 0
   TOP_DOT = 5,       // acc[slot] += Re <v0 | v1>
   TOP_TC = 6,        // 5-qubit dense block on the tensor cores (12-qubit tiles)
-  TOP_PERM = 7       // permutation block (k = 1..3): member y moves to member perm[y]; controls as TOP_DENSE
+  TOP_PERM = 7,      // permutation block (k = 1..3): member y moves to member perm[y]; controls as TOP_DENSE
+  TOP_GRADU = 8      // TOP_GRAD then the 1-qubit matrix (per-batch pool) on both vectors, in one sweep
 };
 
 // 32-byte op descriptor; matrices live in a separate pool.
@@ -296,7 +297,7 @@ struct LaunchEnv {
   uint64_t acc_stride = 0;
 };
 sv_status launch_program(sv_state *s, const DeviceProgram &p, const ProgLayout &L,
-                         const std::vector<uint32_t> &op0s, const LaunchEnv &E);
+                         const std::vector<uint32_t> &op0s, const LaunchEnv &E, cudaStream_t st = nullptr);
 struct Opts {   // all int: hashed as key bytes, so no padding
   int fusion_k, tile_m, L, prec, mode;
   int tc_in_tile = 0;

@@ -554,6 +554,54 @@ __device__ void grad_op(const typename Cx<R>::T *__restrict__ psi,
   block_acc<R>(part, acc + op.slot);
 }
 
+// The adjoint sweep's step for one parametric gate, in one pass over the
+// pairs of both vectors: acc[slot] += Im <lambda | G | psi> (as grad_op,
+// on the vectors after the gate), then both vectors <- U^dagger (the 1-qubit
+// matrix at U: row pairs for complex64, row-major for complex128).
+__device__ __forceinline__ void load_u2(const float2 *U, float2 &u00, float2 &u01, float2 &u10, float2 &u11) {
+  const float4 q0 = __ldg(reinterpret_cast<const float4 *>(U));
+  const float4 q1 = __ldg(reinterpret_cast<const float4 *>(U) + 1);
+  u00 = make_float2(q0.x, q0.z);
+  u10 = make_float2(q0.y, q0.w);
+  u01 = make_float2(q1.x, q1.z);
+  u11 = make_float2(q1.y, q1.w);
+}
+__device__ __forceinline__ void load_u2(const double2 *U, double2 &u00, double2 &u01, double2 &u10, double2 &u11) {
+  u00 = __ldg(U);
+  u01 = __ldg(U + 1);
+  u10 = __ldg(U + 2);
+  u11 = __ldg(U + 3);
+}
+
+template <typename R>
+__device__ void grad_u_op(typename Cx<R>::T *__restrict__ psi, typename Cx<R>::T *__restrict__ lam, int m,
+                          const TileOp &op, const typename Cx<R>::T *__restrict__ U, double *acc) {
+  using C = typename Cx<R>::T;
+  const int t = op.t[0];
+  const uint32_t bit = 1u << t;
+  const uint32_t ngroups = 1u << (m - 1);
+  C u00, u01, u10, u11;
+  load_u2(U, u00, u01, u10, u11);
+  const int gen = op.gen & 0x7;
+  R part = 0;
+  for (uint32_t g = threadIdx.x; g < ngroups; g += blockDim.x) {
+    const uint32_t l0 = ins0(g, t), l1 = l0 | bit;
+    const uint32_t p0 = sw<R>(l0), p1 = sw<R>(l1);
+    const C a0 = psi[p0], a1 = psi[p1], b0 = lam[p0], b1 = lam[p1];
+    switch (gen) {
+      case 1: part += imdot(b0, a1) + imdot(b1, a0); break;                       // X
+      case 2: part += imdot(b0, cmake(a1.y, -a1.x)) + imdot(b1, cmake(-a0.y, a0.x)); break;   // Y
+      case 3: part += imdot(b0, a0) - imdot(b1, a1); break;                       // Z
+      default: part += R(-2) * imdot(b1, a1); break;                              // diag(0, -2)
+    }
+    psi[p0] = cfma(u01, a1, cmul(u00, a0));
+    psi[p1] = cfma(u11, a1, cmul(u10, a0));
+    lam[p0] = cfma(u01, b1, cmul(u00, b0));
+    lam[p1] = cfma(u11, b1, cmul(u10, b0));
+  }
+  block_acc<R>(part, acc + op.slot);
+}
+
 // 16-byte unit u of the tile <-> shared memory (swizzled amplitude slots)
 template <typename R> struct Unit;
 template <> struct Unit<float> {

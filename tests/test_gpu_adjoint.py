@@ -112,3 +112,29 @@ def test_unsupported_parametric_gate(svlib):
     psi, lam = svlib.StateVector(3, "c64").set_basis(0), svlib.StateVector(3, "c64")
     with pytest.raises(N.SvError, match="parametric"):
         svlib.adjoint_grad(psi, lam, c, np.zeros(1), [(0, 1, 1.0)])
+
+
+def test_batched_gradient_graph_replay(svlib, oracle):
+    """SV_MODE_TILED_GRAPH records the batched gradient's launch sequence once
+    and replays it: every call (new parameters each time) agrees with direct
+    launches to FP64 accumulation precision (the per-parameter sums are FP64
+    atomics, whose order differs between any two runs) and matches the
+    oracle."""
+    from paper_2106_13995_gb300 import _native as N
+    n, B = 12, 8
+    h = W.hea(n, 3)
+    terms = W.tfim(n)
+    psis = [svlib.StateVector(n, "c64") for _ in range(B)]
+    lams = [svlib.StateVector(n, "c64") for _ in range(B)]
+    gopt = svlib.options(mode=N.SV_MODE_TILED_GRAPH)
+    for seed in (1, 2, 3):
+        params = W.hea_params(B, h.n_params, seed)
+        for p in psis:
+            p.set_basis(0)
+        ev_g, g_g = svlib.adjoint_grad_batch(psis, lams, h, params, terms, opts=gopt)
+        for p in psis:
+            p.set_basis(0)
+        ev_d, g_d = svlib.adjoint_grad_batch(psis, lams, h, params, terms)
+        assert np.max(np.abs(ev_g - ev_d)) <= 1e-12 and np.max(np.abs(g_g - g_d)) <= 1e-12
+        ev_o, g_o, _ = oracle.adjoint_grad(h, params[0], terms)
+        assert abs(ev_g[0] - ev_o) <= 1e-5 and np.max(np.abs(g_g[0] - g_o)) <= 1e-5
