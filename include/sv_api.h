@@ -185,8 +185,12 @@ sv_status sv_synchronize(sv_state *s);
 /* Apply one k-qubit gate (k = 1..6) with nctrl controls (0..8) in place.
  * matrix: host FP64 2^k x 2^k complex, row-major, interleaved.  If adjoint
  * is nonzero the conjugate transpose is applied.  The matrix is assumed
- * unitary (not checked).  Errors: SV_EINVAL for qubits out of range,
- * duplicated, or controls overlapping targets. */
+ * unitary; libraries built with SV_DEBUG, or any build run with the
+ * environment variable SV_CHECK_UNITARY=1, check max |U^dagger U - I| <=
+ * 1e-10 on the host for this call and for every MATRIX op of a circuit and
+ * reject others with SV_EINVAL before anything is enqueued.  Errors:
+ * SV_EINVAL for qubits out of range, duplicated, controls overlapping
+ * targets, or a failed unitarity check. */
 sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_t *controls,
                         int nctrl, const double *matrix, int adjoint);
 

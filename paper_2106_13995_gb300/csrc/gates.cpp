@@ -5,7 +5,10 @@
 // uses: OpenQASM's U3; RX/RY/RZ = exp(-i theta P / 2); PHASE = diag(1, e^{i l});
 // SX/SY/SW = ((1+i)/2)(I - iP) for P = X, Y, W = (X+Y)/sqrt(2); fSim with
 // cos/sin snapped to 0 below 1e-15 so that fSim(pi/2, .) has exact zeros.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <string>
 
 #include "sv_internal.h"
 
@@ -149,6 +152,9 @@ sv_status circuit_to_gates(const sv_circuit *c, const double *params, int n,
       g.U.resize(d * d);
       const double *m = c->matrices + 2 * op.matrix_offset;
       for (int e = 0; e < d * d; e++) g.U[e] = cd(m[2 * e], m[2 * e + 1]);
+      if (unitarity_checks() && unitarity_error(g.U, k) > kUnitaryTol)
+        return set_error(SV_EINVAL, where + "matrix is not unitary (max |U^dagger U - I| = " +
+                                        std::to_string(unitarity_error(g.U, k)) + ")");
     } else {
       double ang[3] = {op.angles[0], op.angles[1], op.angles[2]};
       if (op.param >= 0) {
@@ -164,6 +170,29 @@ sv_status circuit_to_gates(const sv_circuit *c, const double *params, int n,
     out.push_back(std::move(g));
   }
   return SV_OK;
+}
+
+// max over entries of |U^dagger U - I|
+double unitarity_error(const std::vector<cd> &U, int k) {
+  const int d = 1 << k;
+  double worst = 0;
+  for (int i = 0; i < d; i++)
+    for (int j = 0; j < d; j++) {
+      cd a = 0;
+      for (int r = 0; r < d; r++) a += std::conj(U[(size_t)r * d + i]) * U[(size_t)r * d + j];
+      worst = std::max(worst, std::abs(a - (i == j ? cd(1.0) : cd(0.0))));
+    }
+  return worst;
+}
+
+// on in SV_DEBUG builds, or when the environment sets SV_CHECK_UNITARY=1
+bool unitarity_checks() {
+#ifdef SV_DEBUG
+  return true;
+#else
+  const char *e = std::getenv("SV_CHECK_UNITARY");
+  return e && e[0] == '1';
+#endif
 }
 
 bool propagate_basis(const std::vector<Gate> &gates, uint64_t &index, cd &amp) {

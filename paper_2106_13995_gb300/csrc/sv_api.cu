@@ -784,7 +784,6 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
                         const double *matrix, int adjoint) {
   if (!s || !targets || !matrix) return set_error(SV_EINVAL, "null argument");
   if (k < 1 || k > 6) return set_error(SV_EINVAL, "k must be in [1, 6]");
-  s->basis_known = false;
   if (nctrl < 0 || nctrl > 8 || (nctrl > 0 && !controls)) return set_error(SV_EINVAL, "bad controls");
   uint64_t seen = 0;
   std::vector<int> t(k), c(nctrl);
@@ -798,6 +797,9 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
   const int d = 1 << k;
   std::vector<cd> U((size_t)d * d);
   for (int e = 0; e < d * d; e++) U[e] = cd(matrix[2 * e], matrix[2 * e + 1]);
+  if (unitarity_checks() && unitarity_error(U, k) > kUnitaryTol)
+    return set_error(SV_EINVAL, "matrix is not unitary");
+  s->basis_known = false;
   if (adjoint) U = adjoint_of(U, k);
   bool diag = true;
   for (int r = 0; r < d && diag; r++)

@@ -192,6 +192,10 @@ int gate_generator(int gate);                                // 1=X 2=Y 3=Z 4=di
 sv_status circuit_to_gates(const sv_circuit *c, const double *params, int n,
                            std::vector<Gate> &out, bool keep_params_unfused);
 std::vector<cd> adjoint_of(const std::vector<cd> &U, int k);
+// caller matrices checked for unitarity (SV_DEBUG builds, or SV_CHECK_UNITARY=1)
+constexpr double kUnitaryTol = 1e-10;
+bool unitarity_checks();
+double unitarity_error(const std::vector<cd> &U, int k);
 
 // planner.cpp
 std::vector<Block> fuse(const std::vector<Gate> &gates, int fusion_k);

@@ -515,3 +515,14 @@ extern "C" int basis_propagate(const sv_circuit *c, uint64_t index, uint64_t *ou
   amp_re_im[1] = amp.imag();
   return 1;
 }
+
+// Build a circuit's program through the library's cache on a host-only
+// state (no device work): returns the status, for argument checks.
+extern "C" int build_status(const sv_circuit *c) {
+  sv_state st;
+  st.n = c->n_qubits;
+  st.dt = SV_C64;
+  ProgramRef cp;
+  Opts o;
+  return (int)get_program(&st, c, nullptr, nullptr, &cp, &o);
+}

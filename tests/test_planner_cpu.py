@@ -235,3 +235,24 @@ def test_split_bf16_six_qubit_blocks(emu, oracle):
         want = oracle.run(c)
         assert oracle.infidelity(want, psi) <= 1e-8, c.name
         assert np.max(np.abs(psi - want)) <= 1e-4 * np.max(np.abs(want)), c.name
+
+
+def test_unitarity_check_of_caller_matrices(emu, monkeypatch):
+    """With SV_CHECK_UNITARY=1 a circuit's MATRIX op must be unitary to
+    1e-10 (max |U^dagger U - I|) or planning stops with SV_EINVAL; without
+    it the matrix is taken as given."""
+    from paper_2106_13995_gb300 import sim
+    from paper_2106_13995_gb300 import _native as N
+    emu.build_status.argtypes = [C.c_void_p]
+    rng = np.random.default_rng(1)
+    good = W.random_unitary(2, rng)
+    bad = good.copy()
+    bad[0, 0] += 1e-6
+    for m, want_checked in ((good, N.SV_OK), (bad, N.SV_EINVAL)):
+        c = W.Circuit(4, [W.Op("MATRIX", (0, 2), matrix=m), W.Op("H", (1,))])
+        mm = sim.marshal(c)
+        monkeypatch.setenv("SV_CHECK_UNITARY", "1")
+        assert emu.build_status(C.addressof(mm.c)) == want_checked
+        monkeypatch.delenv("SV_CHECK_UNITARY")
+        c2 = W.Circuit(4, [W.Op("MATRIX", (0, 2), matrix=m), W.Op("X", (1,))])   # a new program
+        assert emu.build_status(C.addressof(sim.marshal(c2).c)) == N.SV_OK
