@@ -120,3 +120,38 @@ def test_grid30_properties(svlib, oracle):
     assert p0 >= 1 - 1e-5, p0
     print(f"grid 30q: |<0|U^-1 U|0>|^2 = {p0:.8f}, norm {s.norm2():.8f}")
     s.close()
+
+
+@pytest.mark.parametrize("n", [33, 34])
+def test_largest_states_ghz(svlib, n):
+    """The largest widths the library takes (34 qubits: 128 GiB of
+    complex64): GHZ = H then a CNOT chain gives <Z_q> = 0 for every q (the
+    reduction's branch for qubits 32 and up included, through the workspace
+    path and the no-alloc entry point), norm 1, the two nonzero amplitudes
+    1/sqrt(2), and samples only at 0 and 2^n - 1."""
+    import ctypes as C
+    import torch
+    from paper_2106_13995_gb300 import _native as N
+    free, _ = torch.cuda.mem_get_info()
+    if free < (8 << n) + (8 << 30):
+        pytest.skip("not enough device memory for this width")
+    s = svlib.StateVector(n, "c64").set_basis(0)
+    c = W.ghz(n)
+    N.check(N.lib().sv_mark_modified(s.h))   # take the tile passes, not the basis-state path
+    s.apply_circuit(c)
+    z = s.z_all()
+    assert np.max(np.abs(z)) <= 1e-6, np.max(np.abs(z))
+    out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    N.check(N.lib().sv_expect_z_all_noalloc(C.c_void_p(s.amps.data_ptr()), n, N.SV_C64,
+                                            C.cast(C.c_void_p(out.data_ptr()), C.POINTER(C.c_double)),
+                                            C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out.cpu().numpy())) <= 1e-6
+    assert abs(s.norm2() - 1) <= 1e-6
+    r = float(np.float32(2 ** -0.5))
+    assert s.amps[0].item() == r and s.amps[2 * ((1 << n) - 1)].item() == r
+    shots = s.sample(2000, 3)
+    assert set(shots.tolist()) <= {0, (1 << n) - 1} and 700 < int(np.sum(shots == 0)) < 1300
+    s.close()
+    del s
+    torch.cuda.empty_cache()

@@ -6,7 +6,7 @@ and its workspace.  Calls in a row share the library's fixed scratch array,
 so each later call also shows that leftovers from the one before do not leak
 into its result.  The same call recorded in a CUDA graph and replayed must
 give the same values.  (States above 32 qubits, which take a second branch
-of the reduction kernel, are not run here: 2^33 amplitudes need 64 GiB.)
+of the reduction kernel, are run by the 33- and 34-qubit GHZ tests.)
 
 This file is named to be collected last."""
 import ctypes as C
