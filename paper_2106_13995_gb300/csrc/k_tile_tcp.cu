@@ -8,16 +8,16 @@
 // accumulation in TMEM (paper Sec. II: a circuit moment is a matrix applied
 // to the state vector).  The kernel is arranged so that HBM, the tensor
 // cores and the CUDA cores work at the same time:
-//   - one persistent CTA per SM runs three independent groups of four
+//   - one persistent CTA per SM runs four independent groups of four
 //     warps; each group owns 128 TMEM columns (A_hi, A_lo, D), one
 //     shared-memory tile buffer, and walks its own sequence of tiles;
-//   - a group loads its next tile into registers (16 x 16 bytes a thread)
-//     while it works on the current one, and writes them to shared memory
-//     after storing the current tile, so every group keeps a tile in flight;
+//   - a group loads its tile, runs the pass's blocks on it and stores it;
+//     while it waits for its loads or its MMAs the other three groups
+//     gather, split and scatter (16 warps per SM: the register file allows
+//     no more, and shared memory no more tile buffers next to the B
+//     operands);
 //   - the B operands of all blocks of the pass are copied into shared memory
-//     once per CTA and stay there for all its tiles;
-//   - while one group waits for its MMAs the others gather, split and
-//     scatter.
+//     once per CTA and stay there for all its tiles.
 // The tile's shared-memory layout keeps each even/odd amplitude pair
 // together (16-byte units) and XORs slot bits 1..3 with tile bits 4..6 and
 // 8..10, so unit loads and stores are conflict-free and a warp's gathers of
@@ -35,7 +35,7 @@
 
 namespace sv {
 
-constexpr int kPGroups = 3;                          // tile groups per CTA
+constexpr int kPGroups = 4;                          // tile groups per CTA
 constexpr uint32_t kPGroupThreads = 128;             // group thread t <-> TMEM lane t
 constexpr int kPThreads = kPGroups * (int)kPGroupThreads;
 constexpr uint32_t kPTileBytes = (1u << kTcTileM) * 8;   // 32 KB
@@ -51,6 +51,8 @@ __host__ __device__ constexpr uint32_t tcp_bars_off(int ntc) {
 __host__ __device__ constexpr uint32_t tcp_smem_bytes(int ntc) {
   return tcp_bars_off(ntc) + 8 * (1 + kPGroups) + 4 * (1 + kPGroups) + 4;
 }
+static_assert(tcp_smem_bytes(kTcpMaxBlocks) + 8 * kPUnits <= 227u * 1024u, "shared memory of a CTA");
+static_assert(kPGroups * 128u <= kPTmemCols, "TMEM columns of a CTA");
 
 // Byte offset of tile amplitude l: pairs (2j, 2j+1) stay together, slot bits
 // 1..3 are XORed with tile bits 4..6 and 8..10 (linear over GF(2)).
@@ -68,6 +70,17 @@ struct TcpTable {
 
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(g + 1), "r"(kPGroupThreads) : "memory");
+}
+// group barrier that also ORs a predicate over the group's threads
+__device__ __forceinline__ bool group_sync_or(int g, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, %2, %3, pi;\n"
+      " selp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(g + 1), "r"(kPGroupThreads)
+      : "memory");
+  return r != 0;
 }
 __device__ __forceinline__ void sts128(uint32_t a, int4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
@@ -103,20 +116,13 @@ struct TcpAddr {
   const uint64_t *trip;         // kPUnits trip parts
 };
 
-__device__ __forceinline__ void tcp_prefetch(const TilePass &P, uint64_t tbase, const TcpAddr &A,
-                                             int4 (&r)[kPUnits]) {
-  const int4 *g0 = reinterpret_cast<const int4 *>(P.v0);   // 16-byte units: offset / 2
-#pragma unroll
-  for (uint32_t i = 0; i < kPUnits; i++) r[i] = __ldcs(g0 + ((tbase | A.thr | A.trip[i]) >> 1));
-}
-
 struct TcpGroup {
   int g;              // group index in the CTA
   uint32_t tid;       // thread index in the group (= TMEM lane)
   uint32_t tmem;      // TMEM address of the group's first column (lane 0)
   uint32_t bar_b;     // mbarrier: every B operand has landed
   uint32_t bar_mma;   // mbarrier of this group's MMAs
-  uint32_t *flag;     // shared: the elected thread's last wait succeeded
+  volatile uint32_t *flag;   // shared: the elected thread could not issue (B never landed)
   bool b_ready;       // (elected thread) bar_b has been observed
   uint32_t done;      // this group's blocks so far (mbarrier parity)
   bool pend_mma;      // (elected thread) MMAs committed but not observed
@@ -143,9 +149,9 @@ __device__ __forceinline__ void tcp_split_store(const float2 (&x)[16], uint32_t 
 }
 
 // One tensor-core block on the tile at shared address `ts`, its B operand at
-// shared address `bs`.  Returns false if a wait ran out (uniform in the group).
+// shared address `bs`.  Returns false in a thread whose wait ran out.
 __device__ __forceinline__ bool tcp_block(const TileOp &op, const uint32_t *soff, const uint32_t *rbit, uint32_t ts,
-                                          uint32_t bs, TcpGroup &G, uint32_t *err) {
+                                          uint32_t bs, TcpGroup &G) {
   uint32_t s0 = 0;   // this thread's row (group of 32 amplitudes)
 #pragma unroll
   for (int i = 0; i < 7; i++) s0 ^= ((G.tid >> i) & 1u) ? rbit[i] : 0u;
@@ -172,7 +178,7 @@ __device__ __forceinline__ bool tcp_block(const TileOp &op, const uint32_t *soff
   group_sync(G.g);
   if (G.tid == 0) {
     tc_fence_after();
-    bool ok = G.b_ready || mbar_wait(G.bar_b, 0, kPSpin);
+    const bool ok = G.b_ready || mbar_wait(G.bar_b, 0, kPSpin);
     G.b_ready = ok;
     if (ok) {
       const uint32_t idesc = instr_desc(1u);   // BF16 A and B, FP32 D, M = 128, N = 64
@@ -186,14 +192,15 @@ __device__ __forceinline__ bool tcp_block(const TileOp &op, const uint32_t *soff
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(G.bar_mma)
                    : "memory");
       G.pend_mma = true;
-      ok = mbar_wait(G.bar_mma, G.done & 1, kPSpin);
-      if (ok) G.pend_mma = false;
+    } else {
+      *G.flag = 1u;   // nothing committed: the group's waits below fail
     }
-    if (!ok) atomicExch(err, 1u);
-    *G.flag = ok ? 1u : 0u;
   }
-  group_sync(G.g);
-  if (!*G.flag) return false;
+  // every thread waits for the MMAs itself (no second barrier); a failed
+  // wait reaches the whole group through the next barrier's OR
+  const bool ok = !*G.flag && mbar_wait(G.bar_mma, G.done & 1, kPSpin);
+  if (!ok) return false;
+  if (G.tid == 0) G.pend_mma = false;
   G.done++;
   tc_fence_after();
 #pragma unroll
@@ -239,6 +246,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     for (int i = 0; i < 1 + kPGroups; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bars + 8 * i));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  if (threadIdx.x < kPGroups) slots[1 + threadIdx.x] = 0u;
   if (threadIdx.x < kPUnits) {
     const uint32_t lt = threadIdx.x * kPGroupThreads * 2;
     s_trip[threadIdx.x] = (lt & segmask) | spread_hi(P, lt & ~segmask);
@@ -271,27 +279,28 @@ __global__ void __launch_bounds__(kPThreads, 1)
   const uint32_t ts = sbase + (uint32_t)g * kPTileBytes;
   const uint32_t lthr = G.tid * 2;
   const TcpAddr A{(lthr & segmask) | spread_hi(P, lthr & ~segmask), s_trip};
-  int4 pf[kPUnits];
-  uint64_t tb = t < ntiles ? tile_base(P, t) : 0;
-  if (t < ntiles) tcp_prefetch(P, tb, A, pf);
   bool failed = false;
   for (; t < ntiles && !failed; t += stride) {
-    // the prefetched tile into the buffer (its last tile was stored before the
-    // barrier that ended the previous iteration)
+    // the tile into the buffer (its last tile was stored before the barrier
+    // that ended the previous iteration); the other groups work meanwhile
+    const uint64_t cur = tile_base(P, t);
+    {
+      const int4 *g0 = reinterpret_cast<const int4 *>(P.v0);
+      int4 v[kPUnits];
 #pragma unroll
-    for (uint32_t i = 0; i < kPUnits; i++) sts128(ts + tcp_swz((G.tid + i * kPGroupThreads) * 2), pf[i]);
-    const uint64_t cur = tb;
-    if (t + stride < ntiles) {
-      tb = tile_base(P, t + stride);
-      tcp_prefetch(P, tb, A, pf);   // in flight while this tile's blocks run
+      for (uint32_t i = 0; i < kPUnits; i++) v[i] = __ldcs(g0 + ((cur | A.thr | A.trip[i]) >> 1));
+#pragma unroll
+      for (uint32_t i = 0; i < kPUnits; i++) sts128(ts + tcp_swz((G.tid + i * kPGroupThreads) * 2), v[i]);
     }
-    for (int oi = 0; oi < P.nops && !failed; oi++) {
-      group_sync(g);
-      if (!tcp_block(P.ops[oi], T.soff[oi], T.rbit[oi], ts, bbase + (uint32_t)oi * kPBBytes, G, P.err))
-        failed = true;
+    bool ok = true;
+    for (int oi = 0; oi < P.nops; oi++) {
+      if (group_sync_or(g, !ok)) break;
+      ok = tcp_block(P.ops[oi], T.soff[oi], T.rbit[oi], ts, bbase + (uint32_t)oi * kPBBytes, G);
     }
-    group_sync(g);
-    if (failed) break;
+    if (group_sync_or(g, !ok)) {
+      failed = true;
+      break;
+    }
     int4 *g0 = reinterpret_cast<int4 *>(P.v0);
 #pragma unroll
     for (uint32_t i = 0; i < kPUnits; i++)
@@ -299,6 +308,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     group_sync(g);
   }
   // no copy or MMA may outlive the CTA
+  if (failed && G.tid == 0) atomicExch(P.err, 1u);
   if (G.tid == 0) {
     if (G.pend_mma) mbar_wait(G.bar_mma, G.done & 1, kPSpin);
     if (g == 0 && ntc > 0) mbar_wait(G.bar_b, 0, kPSpin);
