@@ -82,6 +82,9 @@ __device__ __forceinline__ bool group_sync_or(int g, bool p) {
       : "memory");
   return r != 0;
 }
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
 __device__ __forceinline__ void sts128(uint32_t a, int4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
@@ -280,17 +283,25 @@ __global__ void __launch_bounds__(kPThreads, 1)
   const uint32_t lthr = G.tid * 2;
   const TcpAddr A{(lthr & segmask) | spread_hi(P, lthr & ~segmask), s_trip};
   bool failed = false;
+  uint64_t cur = t < ntiles ? tile_base(P, t) : 0;
   for (; t < ntiles && !failed; t += stride) {
     // the tile into the buffer (its last tile was stored before the barrier
     // that ended the previous iteration); the other groups work meanwhile
-    const uint64_t cur = tile_base(P, t);
+    const int4 *g0 = reinterpret_cast<const int4 *>(P.v0);
     {
-      const int4 *g0 = reinterpret_cast<const int4 *>(P.v0);
       int4 v[kPUnits];
 #pragma unroll
       for (uint32_t i = 0; i < kPUnits; i++) v[i] = __ldcs(g0 + ((cur | A.thr | A.trip[i]) >> 1));
 #pragma unroll
       for (uint32_t i = 0; i < kPUnits; i++) sts128(ts + tcp_swz((G.tid + i * kPGroupThreads) * 2), v[i]);
+    }
+    // the group's next tile towards L2 while this one's blocks run, so its
+    // load waits on L2 rather than on HBM
+    uint64_t nxt = 0;
+    if (t + stride < ntiles) {
+      nxt = tile_base(P, t + stride);
+#pragma unroll
+      for (uint32_t i = 0; i < kPUnits; i++) prefetch_l2(g0 + ((nxt | A.thr | A.trip[i]) >> 1));
     }
     bool ok = true;
     for (int oi = 0; oi < P.nops; oi++) {
@@ -301,10 +312,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
       failed = true;
       break;
     }
-    int4 *g0 = reinterpret_cast<int4 *>(P.v0);
+    int4 *o0 = reinterpret_cast<int4 *>(P.v0);
 #pragma unroll
     for (uint32_t i = 0; i < kPUnits; i++)
-      __stcs(g0 + ((cur | A.thr | A.trip[i]) >> 1), lds128(ts + tcp_swz((G.tid + i * kPGroupThreads) * 2)));
+      __stcs(o0 + ((cur | A.thr | A.trip[i]) >> 1), lds128(ts + tcp_swz((G.tid + i * kPGroupThreads) * 2)));
+    cur = nxt;
     group_sync(g);
   }
   // no copy or MMA may outlive the CTA
