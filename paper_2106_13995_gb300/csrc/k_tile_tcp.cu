@@ -30,6 +30,8 @@
 // copies and frees its TMEM.
 #include <algorithm>
 #include <cstring>
+#include <string>
+#include <vector>
 
 #include "tile_ops.cuh"
 
@@ -64,8 +66,11 @@ __host__ __device__ constexpr uint32_t tcp_swz(uint32_t l) {
 // parameter block (warp-uniform reads): each block's member offsets
 // tcp_swz(target bits of y) and the offset contributed by each row bit.
 struct TcpTable {
-  uint32_t soff[kTcpMaxBlocks][32];
+  uint32_t soff[kTcpMaxBlocks][32];   // gather: the block's own layout
   uint32_t rbit[kTcpMaxBlocks][8];
+  uint32_t doff[kTcpMaxBlocks][32];   // scatter: the next block's layout (the store's after the last)
+  uint32_t dbit[kTcpMaxBlocks][8];
+  uint32_t flags[kTcpMaxBlocks];      // bit 0: gather member pairs, bit 1: scatter member pairs
 };
 
 __device__ __forceinline__ void group_sync(int g) {
@@ -151,15 +156,18 @@ __device__ __forceinline__ void tcp_split_store(const float2 (&x)[16], uint32_t 
   tmem_st16x(taddr + 32, lo);
 }
 
-// One tensor-core block on the tile at shared address `ts`, its B operand at
-// shared address `bs`.  Returns false in a thread whose wait ran out.
-__device__ __forceinline__ bool tcp_block(const TileOp &op, const uint32_t *soff, const uint32_t *rbit, uint32_t ts,
-                                          uint32_t bs, TcpGroup &G) {
+// One tensor-core block (op i of table T) on the tile at shared address
+// `ts`, its B operand at shared address `bs`: gathered from the tile in the
+// block's layout, scattered back in the next one's.  Returns false in a
+// thread whose wait ran out.
+__device__ __forceinline__ bool tcp_block(const TcpTable &T, int i, uint32_t ts, uint32_t bs, TcpGroup &G) {
+  const uint32_t *soff = T.soff[i], *rbit = T.rbit[i];
   uint32_t s0 = 0;   // this thread's row (group of 32 amplitudes)
 #pragma unroll
-  for (int i = 0; i < 7; i++) s0 ^= ((G.tid >> i) & 1u) ? rbit[i] : 0u;
+  for (int b = 0; b < 7; b++) s0 ^= ((G.tid >> b) & 1u) ? rbit[b] : 0u;
   const uint32_t lane = (G.tid & ~31u) << 16;         // the warp's TMEM lane quadrant
-  const bool pairs = op.t[0] == 0;                    // member pairs (y, y + 1) share a 16-byte unit
+  const uint32_t flags = T.flags[i];
+  bool pairs = flags & 1u;                            // member pairs (y, y + 1) share a 16-byte unit
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     float2 x[16];
@@ -206,6 +214,14 @@ __device__ __forceinline__ bool tcp_block(const TileOp &op, const uint32_t *soff
   if (G.tid == 0) G.pend_mma = false;
   G.done++;
   tc_fence_after();
+  {
+    const uint32_t *dbit = T.dbit[i];
+    soff = T.doff[i];
+    s0 = 0;
+#pragma unroll
+    for (int b = 0; b < 7; b++) s0 ^= ((G.tid >> b) & 1u) ? dbit[b] : 0u;
+    pairs = flags & 2u;
+  }
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     uint32_t r[32];
@@ -306,7 +322,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     bool ok = true;
     for (int oi = 0; oi < P.nops; oi++) {
       if (group_sync_or(g, !ok)) break;
-      ok = tcp_block(P.ops[oi], T.soff[oi], T.rbit[oi], ts, bbase + (uint32_t)oi * kPBBytes, G);
+      ok = tcp_block(T, oi, ts, bbase + (uint32_t)oi * kPBBytes, G);
     }
     if (group_sync_or(g, !ok)) {
       failed = true;
@@ -332,31 +348,138 @@ __global__ void __launch_bounds__(kPThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(slots[0]), "r"(kPTmemCols));
 }
 
-// Thread-index bits of a block's rows (host): the lane bits first take tile
-// bits that reach distinct bank groups under tcp_swz -- with 8-byte gathers
-// one bit from each of the classes {0}, {1,4,8}, {2,5,9}, {3,6,10}; with
-// 16-byte pair gathers (tile bit 0 a target) one from each of the last three
-// -- then the remaining free bits follow in increasing order.
-void tcp_row_positions(TileOp &op) {
-  uint32_t targets = 0;
-  for (int j = 0; j < op.k; j++) targets |= 1u << op.t[j];
-  static const int kClass[4][3] = {{0, -1, -1}, {1, 4, 8}, {2, 5, 9}, {3, 6, 10}};
-  int P[12], np = 0;
-  uint32_t used = targets;
-  for (int c = (targets & 1u) ? 1 : 0; c < 4; c++)
-    for (int p : kClass[c])
-      if (p >= 0 && !((used >> p) & 1u)) {
-        P[np++] = p;
-        used |= 1u << p;
+// Tile position p under the layout with pair bit pb: bits 0 and pb swapped.
+static inline uint32_t tcp_layout_pos(uint32_t p, uint32_t pb) { return p == pb ? 0u : (p == 0 ? pb : p); }
+static inline uint32_t tcp_layout(uint32_t l, uint32_t pb) {
+  if (pb == 0) return l;
+  const uint32_t b0 = l & 1u, bp = (l >> pb) & 1u;
+  return (l & ~(1u | (1u << pb))) | bp | (b0 << pb);
+}
+
+// Thread-index bits of a block's rows (host).  A warp's shared-memory
+// accesses are conflict-free when its lanes reach distinct banks: under
+// tcp_swz the bank of slot s (8-byte granule) is given by slot bits 0..3
+// after bits 1..3 take the XOR of bits 4..6 and 8..10, so slot bit p
+// contributes the vector e0 (p = 0), e1 (p in {1,4,8}), e2 ({2,5,9}),
+// e3 ({3,6,10}) or nothing (7, 11).  8-byte moves want lane bits 0..3 to
+// contribute four independent vectors (16 lanes per wavefront), 16-byte
+// pair moves lane bits 0..2 three independent ones among e1..e3.  The
+// block gathers under the layout with pair bit pg and scatters under the
+// one with pair bit ps; the lane bits are picked among its row bits so that
+// both are conflict-free where possible (gather first), then the remaining
+// row bits follow in increasing order.
+static uint32_t tcp_bank_vec(uint32_t slot) {
+  static const uint32_t kVec[12] = {1u, 2u, 4u, 8u, 2u, 4u, 8u, 0u, 2u, 4u, 8u, 0u};
+  return slot < 12 ? kVec[slot] : 0u;
+}
+// true when the k vectors (restricted to mask) are linearly independent over GF(2)
+static bool tcp_independent(const uint32_t *v, int k, uint32_t mask) {
+  uint32_t basis[4] = {0, 0, 0, 0};   // basis[b]: a kept vector whose top bit is b
+  for (int i = 0; i < k; i++) {
+    uint32_t x = v[i] & mask;
+    for (int b = 3; b >= 0; b--) {
+      if (!((x >> b) & 1u)) continue;
+      if (!basis[b]) {
+        basis[b] = x;
         break;
       }
-  for (int p = 0; p < kTcTileM; p++)
-    if (!((used >> p) & 1u)) {
-      P[np++] = p;
-      used |= 1u << p;
+      x ^= basis[b];
     }
+    if (x == 0) return false;
+  }
+  return true;
+}
+void tcp_row_positions(TileOp &op, int pair_gather, int pair_scatter) {
+  const uint32_t pg = (uint32_t)pair_gather, ps = (uint32_t)pair_scatter;
+  uint32_t targets = 0;
+  for (int j = 0; j < op.k; j++) targets |= 1u << op.t[j];
+  int rows[12], nr = 0;
+  for (int p = 0; p < kTcTileM; p++)
+    if (!((targets >> p) & 1u)) rows[nr++] = p;
+  const bool gpair = tcp_layout_pos(op.t[0], pg) == 0, spair = tcp_layout_pos(op.t[0], ps) == 0;
+  const int kg = gpair ? 3 : 4, ks = spair ? 3 : 4;
+  const uint32_t mg = gpair ? 0xEu : 0xFu, ms = spair ? 0xEu : 0xFu;
+  int best[4] = {0, 1, 2, 3}, best_score = -1;
+  const int K = nr < 4 ? nr : 4;
+  int sel[4];
+  // ordered choices of K lane positions among the row bits
+  for (sel[0] = 0; sel[0] < nr; sel[0]++)
+    for (sel[1] = 0; sel[1] < nr; sel[1]++)
+      for (sel[2] = 0; sel[2] < nr; sel[2]++)
+        for (sel[3] = 0; sel[3] < nr; sel[3]++) {
+          bool distinct = true;
+          for (int x = 0; x < K; x++)
+            for (int y = 0; y < x; y++) distinct &= sel[x] != sel[y];
+          if (!distinct) continue;
+          uint32_t vg[4], vs[4];
+          for (int x = 0; x < K; x++) {
+            vg[x] = tcp_bank_vec(tcp_layout_pos((uint32_t)rows[sel[x]], pg));
+            vs[x] = tcp_bank_vec(tcp_layout_pos((uint32_t)rows[sel[x]], ps));
+          }
+          const int score = (tcp_independent(vg, std::min(kg, K), mg) ? 2 : 0) +
+                            (tcp_independent(vs, std::min(ks, K), ms) ? 1 : 0);
+          if (score > best_score) {
+            best_score = score;
+            for (int x = 0; x < K; x++) best[x] = sel[x];
+          }
+        }
+  int P[12], np = 0;
+  uint32_t used = 0;
+  for (int x = 0; x < K; x++) {
+    P[np++] = rows[best[x]];
+    used |= 1u << rows[best[x]];
+  }
+  for (int i = 0; i < nr; i++)
+    if (!((used >> rows[i]) & 1u)) P[np++] = rows[i];
   std::memset(op.tbpos, 0, sizeof(op.tbpos));
   for (int i = 0; i < np && i < 9; i++) op.tbpos[i >> 1] |= (uint8_t)(P[i] << (4 * (i & 1)));
+}
+
+// Host replay of a pipelined pass's shared-memory addressing (the tables
+// launch_tile_tcp builds): tile amplitudes carry their own index as a
+// label; the load, every block's gather and scatter, and the store follow
+// the kernel's offsets.  Returns "" when every gathered member is the
+// amplitude the block's row and member index name, every scatter fills
+// all 4096 slots, pair moves are 16-byte aligned units, and the store
+// finds each amplitude at its place; else what failed.
+static void tcp_build_table(const TilePass &p, const HostPass &host, TcpTable &tab);
+std::string tcp_layout_selftest(const TilePass &p, const HostPass &host) {
+  if (!tcp_pass_ok(p, host)) return "not a pure tensor-core pass";
+  TcpTable T;
+  tcp_build_table(p, host, T);
+  const uint32_t NT = 1u << kTcTileM;
+  std::vector<int32_t> slot(NT, -1), next(NT);
+  for (uint32_t l = 0; l < NT; l++) slot[tcp_swz(l) / 8] = (int32_t)l;
+  for (int i = 0; i < p.nops; i++) {
+    const TileOp &op = host.ops[i];
+    std::fill(next.begin(), next.end(), -1);
+    for (uint32_t tid = 0; tid < kPGroupThreads; tid++) {
+      uint32_t s0 = 0, d0 = 0, row = 0;
+      for (int b = 0; b < 7; b++)
+        if ((tid >> b) & 1u) {
+          s0 ^= T.rbit[i][b];
+          d0 ^= T.dbit[i][b];
+          row |= 1u << ((op.tbpos[b >> 1] >> (4 * (b & 1))) & 15u);
+        }
+      for (int y = 0; y < 32; y++) {
+        uint32_t l = row;
+        for (int j = 0; j < 5; j++) l |= (uint32_t)((y >> j) & 1) << op.t[j];
+        const uint32_t ga = s0 ^ T.soff[i][y], sa = d0 ^ T.doff[i][y];
+        if (ga >= NT * 8 || sa >= NT * 8) return "offset outside the tile";
+        if ((T.flags[i] & 1u) && (y & 1) == 0 && (ga % 16 != 0 || T.soff[i][y + 1] != T.soff[i][y] + 8))
+          return "gather pair not a 16-byte unit";
+        if ((T.flags[i] & 2u) && (y & 1) == 0 && (sa % 16 != 0 || T.doff[i][y + 1] != T.doff[i][y] + 8))
+          return "scatter pair not a 16-byte unit";
+        if (slot[ga / 8] != (int32_t)l) return "block " + std::to_string(i) + " gathers the wrong amplitude";
+        if (next[sa / 8] != -1) return "block " + std::to_string(i) + " scatters twice to one slot";
+        next[sa / 8] = (int32_t)l;
+      }
+    }
+    slot.swap(next);
+  }
+  for (uint32_t l = 0; l < NT; l++)
+    if (slot[tcp_swz(l) / 8] != (int32_t)l) return "the store finds the wrong amplitude";
+  return "";
 }
 
 bool tcp_pass_ok(const TilePass &p, const HostPass &host) {
@@ -374,20 +497,34 @@ sv_status launch_tile_tcp(sv_state *s, const TilePass &p, const HostPass &host, 
   const uint64_t per_cta = (uint64_t)kPGroups;
   const int grid = (int)std::min<uint64_t>((ntiles + per_cta - 1) / per_cta, (uint64_t)s->sm_count);
   TcpTable tab;
-  std::memset(&tab, 0, sizeof(tab));
-  for (int i = 0; i < p.nops; i++) {
-    const TileOp &op = host.ops[i];
-    for (int y = 0; y < 32; y++) {
-      uint32_t l = 0;
-      for (int j = 0; j < 5; j++) l |= (uint32_t)((y >> j) & 1) << op.t[j];
-      tab.soff[i][y] = tcp_swz(l);
-    }
-    for (int b = 0; b < 7; b++) tab.rbit[i][b] = tcp_swz(1u << ((op.tbpos[b >> 1] >> (4 * (b & 1))) & 15u));
-  }
+  tcp_build_table(p, host, tab);
   k_tile_tcp<<<grid, kPThreads, tcp_smem_bytes(p.nops), stream>>>(p, tab);
   g_launches++;
   SV_CUDA(cudaGetLastError());
   return SV_OK;
+}
+
+// The per-block tables of a pass: member and row-bit offsets under the
+// block's layout (gather) and the next block's (scatter), and pair flags.
+static void tcp_build_table(const TilePass &p, const HostPass &host, TcpTable &tab) {
+  std::memset(&tab, 0, sizeof(tab));
+  for (int i = 0; i < p.nops; i++) {
+    const TileOp &op = host.ops[i];
+    const uint32_t pg = (uint32_t)tcp_pair_bit(host.ops, p.nops, i);       // this block's layout
+    const uint32_t ps = (uint32_t)tcp_pair_bit(host.ops, p.nops, i + 1);   // the next one's
+    for (int y = 0; y < 32; y++) {
+      uint32_t l = 0;
+      for (int j = 0; j < 5; j++) l |= (uint32_t)((y >> j) & 1) << op.t[j];
+      tab.soff[i][y] = tcp_swz(tcp_layout(l, pg));
+      tab.doff[i][y] = tcp_swz(tcp_layout(l, ps));
+    }
+    for (int b = 0; b < 7; b++) {
+      const uint32_t r = 1u << ((op.tbpos[b >> 1] >> (4 * (b & 1))) & 15u);
+      tab.rbit[i][b] = tcp_swz(tcp_layout(r, pg));
+      tab.dbit[i][b] = tcp_swz(tcp_layout(r, ps));
+    }
+    tab.flags[i] = (tcp_layout_pos(op.t[0], pg) == 0 ? 1u : 0u) | (tcp_layout_pos(op.t[0], ps) == 0 ? 2u : 0u);
+  }
 }
 
 }  // namespace sv

@@ -202,6 +202,43 @@ void put_pairs_c64(std::vector<uint8_t> &pool, const cd *U, int k) {
 }
 
 // Convert one planned pass into TilePass + TileOps (+ matrices).
+// First targets (tile positions) of the blocks of a pass the pipelined
+// tensor-core kernel runs.  Block j > 0 is gathered under a layout whose
+// pair bit is its first target c_j; it scatters in 16-byte pairs when
+// c_j = c_{j+1} (the last block and the store: when c_j = 0), and block 0
+// gathers in pairs when c_0 = 0.  Pick c_j among each block's targets to
+// maximise those cases (dynamic programming over at most 6 x 5 choices;
+// ties go to the lowest tile position).
+static std::vector<int> tcp_first_targets(const std::vector<std::vector<int>> &T) {
+  const int n = (int)T.size();
+  std::vector<std::vector<int>> score(n), from(n);
+  for (int j = 0; j < n; j++) {
+    score[j].assign(T[j].size(), 0);
+    from[j].assign(T[j].size(), -1);
+    for (size_t a = 0; a < T[j].size(); a++) {
+      int best = j == 0 ? (T[0][a] == 0 ? 1 : 0) : -1;
+      if (j > 0)
+        for (size_t c = 0; c < T[j - 1].size(); c++) {
+          const int v = score[j - 1][c] + (T[j - 1][c] == T[j][a] ? 1 : 0);
+          if (v > best) {
+            best = v;
+            from[j][a] = (int)c;
+          }
+        }
+      score[j][a] = best + (j == n - 1 && T[j][a] == 0 ? 1 : 0);
+    }
+  }
+  std::vector<int> c(n);
+  int a = 0;
+  for (size_t x = 1; x < T[n - 1].size(); x++)
+    if (score[n - 1][x] > score[n - 1][a]) a = (int)x;
+  for (int j = n - 1; j >= 0; j--) {
+    c[j] = T[j][a];
+    a = from[j][a];
+  }
+  return c;
+}
+
 sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
                            std::vector<uint32_t> &op0s, const std::vector<int> &batch_mat_off) {
   TilePass tp;
@@ -220,6 +257,21 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
     if (loc[q] < 0) tp.out_pos[no++] = (int8_t)q;
   op0s.push_back((uint32_t)prog.ops.size());
   const size_t ab = amp_bytes(b.dt);
+  // a pass for the pipelined tensor-core kernel: its blocks' first targets
+  std::vector<int> tc_first;
+  {
+    bool pure = tp.m == kTcTileM && !P.ops.empty() && P.ops.size() <= (size_t)kTcpMaxBlocks;
+    std::vector<std::vector<int>> T;
+    for (const Block &blk : P.ops) {
+      pure = pure && blk.kind == TOP_TC && blk.qubits.size() == 5;
+      if (!pure) break;
+      std::vector<int> t;
+      for (int q : blk.qubits) t.push_back(loc[q]);
+      std::sort(t.begin(), t.end());
+      T.push_back(t);
+    }
+    if (pure) tc_first = tcp_first_targets(T);
+  }
   for (size_t bi = 0; bi < P.ops.size(); bi++) {
     const Block &blk = P.ops[bi];
     // the adjoint sweep's probe of a parametric gate directly followed by
@@ -294,12 +346,18 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
         }
       }
     } else if (op.kind == TOP_TC) {
-      // targets in increasing tile position (tile bit 0, if a target, is the
-      // first: the pipelined kernel then gathers member pairs), U permuted
-      // to match; rows of the GEMM on the free tile bits, lane bits chosen
-      // to spread a warp's gathers over the banks
+      // targets in increasing tile position, except that in a pipelined
+      // pass the block's chosen first target leads (member pairs (y, y+1)
+      // then differ in it); U permuted to match; rows of the GEMM on the
+      // free tile bits, lane bits chosen to spread a warp's gathers over the
+      // banks of the layout the block is gathered under
+      const int jop = (int)(prog.ops.size() - op0s.back());
+      const int first = tc_first.empty() ? -1 : tc_first[jop];
       int ord[6] = {0, 1, 2, 3, 4, 5};
-      std::sort(ord, ord + op.k, [&](int a, int c) { return op.t[a] < op.t[c]; });
+      std::sort(ord, ord + op.k, [&](int a, int c) {
+        if ((op.t[a] == first) != (op.t[c] == first)) return op.t[a] == first;
+        return op.t[a] < op.t[c];
+      });
       uint8_t tsorted[6];
       for (int j = 0; j < op.k; j++) tsorted[j] = op.t[ord[j]];
       for (int j = 0; j < op.k; j++) op.t[j] = tsorted[j];
@@ -312,7 +370,8 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
       };
       for (int r = 0; r < d; r++)
         for (int c = 0; c < d; c++) Up[(size_t)r * d + c] = blk.U[(size_t)from_sorted(r) * d + from_sorted(c)];
-      tcp_row_positions(op);
+      const int next_pair = tc_first.empty() || jop + 1 >= (int)tc_first.size() ? 0 : tc_first[jop + 1];
+      tcp_row_positions(op, tc_first.empty() || jop == 0 ? 0 : first, next_pair);
       while (prog.mats.size() % 16) prog.mats.push_back(0);
       op.mat = (uint32_t)(prog.mats.size() / ab);
       std::vector<uint32_t> packed;

@@ -457,8 +457,21 @@ constexpr int kTcpMaxBlocks = 6;
 sv_status launch_tile_tcp(sv_state *s, const TilePass &p, const HostPass &host, cudaStream_t stream);
 // a pass the pipelined kernel runs: 12-qubit tiles, 1..kTcpMaxBlocks ops, all 5-qubit TOP_TC
 bool tcp_pass_ok(const TilePass &p, const HostPass &host);
-// plan-time row map of a TOP_TC op for the pipelined kernel's bank layout
-void tcp_row_positions(TileOp &op);
+// The pipelined kernel gives block j of a pass its own shared-memory layout:
+// tile bits 0 and pair_bit swapped, where pair_bit is 0 for the first block
+// (and for the tile store after the last) and the block's first target
+// op.t[0] for the others, so that those blocks gather member pairs (y, y+1)
+// as 16-byte units, and a block whose first target is the next layout's
+// pair bit scatters them the same way.
+inline int tcp_pair_bit(const TileOp *ops, int nops, int j) {
+  return (j <= 0 || j >= nops) ? 0 : (int)ops[j].t[0];
+}
+// plan-time row map of a TOP_TC op for the pipelined kernel's bank layout,
+// for a block gathered under the layout with pair bit pair_gather and
+// scattered under the one with pair bit pair_scatter
+void tcp_row_positions(TileOp &op, int pair_gather, int pair_scatter);
+// host replay of a pipelined pass's shared-memory addressing; "" when sound
+std::string tcp_layout_selftest(const TilePass &p, const HostPass &host);
 // tensor-core 5-qubit block (k_tc.cu)
 size_t tc_matrix_words(sv_prec mode, int k);
 void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t> &out);

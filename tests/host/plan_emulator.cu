@@ -399,7 +399,14 @@ extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure,
       continue;
     }
     const HostPass hp{prog.ops.data() + cp->op0s[pi], prog.mats.data()};
-    *npure += tcp_pass_ok(tp, hp) ? 1 : 0;
+    if (tcp_pass_ok(tp, hp)) {
+      (*npure)++;
+      const std::string why = tcp_layout_selftest(tp, hp);
+      if (!why.empty()) {
+        std::printf("pass %zu layouts: %s\n", pi, why.c_str());
+        return -1;
+      }
+    }
     const uint32_t TS = 1u << tp.m;
     // decode every op's matrix once
     std::vector<std::vector<cx>> Us(tp.nops);
@@ -412,7 +419,9 @@ extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure,
         if (op.k != 5) { std::printf("tensor-core block with %d targets\n", op.k); return -1; }
         uint32_t tmask = 0;
         for (int j = 0; j < 5; j++) {
-          if (j > 0 && op.t[j] <= op.t[j - 1]) { std::printf("targets not increasing\n"); return -1; }
+          // the first target may be any (the pass's layout chain picks it), the rest increase
+          if (j > 1 && op.t[j] <= op.t[j - 1]) { std::printf("targets not increasing\n"); return -1; }
+          if ((tmask >> op.t[j]) & 1u) { std::printf("repeated target\n"); return -1; }
           tmask |= 1u << op.t[j];
         }
         uint32_t rows = 0;
