@@ -441,12 +441,17 @@ void tcp_row_positions(TileOp &op, int pair_gather, int pair_scatter) {
 // the kernel's offsets.  Returns "" when every gathered member is the
 // amplitude the block's row and member index name, every scatter fills
 // all 4096 slots, pair moves are 16-byte aligned units, and the store
-// finds each amplitude at its place; else what failed.
+// finds each amplitude at its place; else what failed.  Adds the pass's
+// blocks that gather / scatter in 16-byte pairs to the counters given.
 static void tcp_build_table(const TilePass &p, const HostPass &host, TcpTable &tab);
-std::string tcp_layout_selftest(const TilePass &p, const HostPass &host) {
+std::string tcp_layout_selftest(const TilePass &p, const HostPass &host, int *pair_gathers, int *pair_scatters) {
   if (!tcp_pass_ok(p, host)) return "not a pure tensor-core pass";
   TcpTable T;
   tcp_build_table(p, host, T);
+  for (int i = 0; i < p.nops; i++) {
+    if (pair_gathers) *pair_gathers += (int)(T.flags[i] & 1u);
+    if (pair_scatters) *pair_scatters += (int)((T.flags[i] >> 1) & 1u);
+  }
   const uint32_t NT = 1u << kTcTileM;
   std::vector<int32_t> slot(NT, -1), next(NT);
   for (uint32_t l = 0; l < NT; l++) slot[tcp_swz(l) / 8] = (int32_t)l;

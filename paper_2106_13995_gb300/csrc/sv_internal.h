@@ -471,7 +471,8 @@ inline int tcp_pair_bit(const TileOp *ops, int nops, int j) {
 // scattered under the one with pair bit pair_scatter
 void tcp_row_positions(TileOp &op, int pair_gather, int pair_scatter);
 // host replay of a pipelined pass's shared-memory addressing; "" when sound
-std::string tcp_layout_selftest(const TilePass &p, const HostPass &host);
+std::string tcp_layout_selftest(const TilePass &p, const HostPass &host, int *pair_gathers = nullptr,
+                                int *pair_scatters = nullptr);
 // tensor-core 5-qubit block (k_tc.cu)
 size_t tc_matrix_words(sv_prec mode, int k);
 void tc_pack_matrix(const std::vector<cd> &U, sv_prec mode, std::vector<uint32_t> &out);

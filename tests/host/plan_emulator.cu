@@ -354,6 +354,14 @@ static std::vector<std::complex<double>> unpack_embedding(const uint8_t *base, i
   return U;
 }
 
+// blocks of the pipelined passes emulated so far that move 16-byte pairs
+static int g_pair_gathers = 0, g_pair_scatters = 0;
+extern "C" void tc_pair_counts(int *gathers, int *scatters) {
+  *gathers = g_pair_gathers;
+  *scatters = g_pair_scatters;
+  g_pair_gathers = g_pair_scatters = 0;
+}
+
 extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure, int fusion_k, int *nsix) {
   typedef std::complex<double> cx;
   sv_state st;
@@ -401,7 +409,7 @@ extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure,
     const HostPass hp{prog.ops.data() + cp->op0s[pi], prog.mats.data()};
     if (tcp_pass_ok(tp, hp)) {
       (*npure)++;
-      const std::string why = tcp_layout_selftest(tp, hp);
+      const std::string why = tcp_layout_selftest(tp, hp, &g_pair_gathers, &g_pair_scatters);
       if (!why.empty()) {
         std::printf("pass %zu layouts: %s\n", pi, why.c_str());
         return -1;

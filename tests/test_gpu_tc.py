@@ -72,6 +72,29 @@ def test_circuits_with_fused_5q_blocks(svlib, oracle, mode, tile_m):
         print(f"{c.name} {mode} m={tile_m}: blocks {nb}, passes {npass}, 1-F {inf:.2e}, max|d| {amp:.2e}")
 
 
+def test_pipelined_layout_chains(svlib, oracle):
+    """Chains of dense 5-qubit blocks with overlapping targets, split-BF16:
+    the pipelined tile pass with a shared-memory layout per block (16-byte
+    pair gathers and scatters), checked amplitude by amplitude against the
+    FP64 oracle from a random state; the error budget grows with the
+    number of blocks."""
+    for seed, (n, count, span) in enumerate([(13, 12, 7), (14, 16, 8), (16, 24, 9), (18, 20, 12)]):
+        rng = np.random.default_rng(seed)
+        c = W.block_chain(n, count, seed + 40, span)
+        psi0 = W.random_state(n, rng)
+        s = svlib.StateVector(n, "c64").load(psi0)
+        opts = svlib.options(prec=MODES["bf16x3"])
+        nb, npass = s.plan_info(c, opts=opts)
+        s.apply_circuit(c, opts=opts)
+        want = oracle.run(c, psi0.astype(np.complex64).astype(np.complex128))
+        inf, amp = fidelity_metrics(want, s.numpy())
+        scale = np.max(np.abs(want))
+        print(f"{c.name}: blocks {nb}, passes {npass}, 1-F {inf:.2e}, max|d| {amp / scale:.2e} of max|a|")
+        assert amp <= nb * AMP_TOL["bf16x3"] * scale, (c.name, amp, scale)
+        assert inf <= 1e-6, (c.name, inf)
+        s.close()
+
+
 def test_tc_rejected_for_complex128(svlib, oracle):
     """complex128 states keep FP64 CUDA-core arithmetic in every mode."""
     c = W.random_u3_cz(13, 4, 1)

@@ -172,6 +172,38 @@ def test_split_bf16_programs_match_oracle(emu, oracle):
         assert np.max(np.abs(psi - want)) <= 1e-4 * np.max(np.abs(want)), c.name
 
 
+def test_pipelined_layout_chains(emu, oracle):
+    """Passes of dense 5-qubit blocks whose targets overlap: every pass runs
+    in the pipelined kernel, whose blocks after the first see the tile
+    through their own shared-memory layout.  The emulator replays the
+    kernel's address tables for every pass (each gathered member must be
+    the amplitude its row and member index name, each scatter must fill
+    every slot once, pair moves must be aligned 16-byte units) and runs the
+    program against the FP64 oracle; over these circuits both 16-byte pair
+    gathers and pair scatters must occur."""
+    from paper_2106_13995_gb300 import sim
+    emu.tc_program_emulate.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
+    emu.tc_pair_counts.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    g, sc = C.c_int(), C.c_int()
+    emu.tc_pair_counts(C.byref(g), C.byref(sc))   # reset
+    total_g = total_s = 0
+    for seed, (n, count, span) in enumerate([(13, 12, 7), (14, 16, 8), (12, 10, 12), (15, 14, 9)]):
+        c = W.block_chain(n, count, seed + 40, span)
+        mm = sim.marshal(c)
+        psi = np.zeros(1 << n, dtype=np.complex128)
+        psi[0] = 1
+        npure, nsix = C.c_int(), C.c_int()
+        npass = emu.tc_program_emulate(C.addressof(mm.c), psi.ctypes.data, C.byref(npure), 0, C.byref(nsix))
+        assert npass > 0 and npure.value == npass, (c.name, npure.value, npass)
+        emu.tc_pair_counts(C.byref(g), C.byref(sc))
+        total_g += g.value
+        total_s += sc.value
+        want = oracle.run(c)
+        assert oracle.infidelity(want, psi) <= 1e-8, c.name
+        assert np.max(np.abs(psi - want)) <= 1e-4 * np.max(np.abs(want)), c.name
+    assert total_g > 0 and total_s > 0, (total_g, total_s)
+
+
 def test_basis_propagation_matches_oracle(emu, oracle):
     """The host-side basis-state path: through the multiplier (X, CNOT,
     Toffoli, C^3X) every basis input |a, b, 0, 0> goes to |a, b, a*b, 0> with

@@ -129,6 +129,20 @@ def random_u3_cz(n: int, layers: int, seed) -> Circuit:
     return c
 
 
+def block_chain(n: int, count: int, seed, span: int = 8) -> Circuit:
+    """count dense 5-qubit blocks (Haar-random unitaries), each on 5 qubits
+    drawn without replacement from a window of `span` consecutive qubits
+    placed at random in the register, so that neighbouring blocks share
+    targets and several blocks fit one tile pass."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(n, name=f"chain_{n}q_{count}b")
+    for _ in range(count):
+        lo = int(rng.integers(0, n - span + 1))
+        t = tuple(int(x) for x in rng.choice(np.arange(lo, lo + span), size=5, replace=False))
+        c.ops.append(Op("MATRIX", t, matrix=random_unitary(5, rng)))
+    return c
+
+
 # ---------------------------------------------------------------------------
 # grid random ("supremacy-style") circuits
 # ---------------------------------------------------------------------------
