@@ -729,7 +729,7 @@ def main():
                                "circuits": len(circs), "widths": "10..24", "depth": 40,
                                "gates": int(sum(len(c.ops) for c in circs)),
                                "launch": "one CUDA graph per call: a persistent cooperative launch for states "
-                                         "whose passes have < 2 tiles per SM, full-grid tile launches for the "
+                                         "whose passes have fewer tiles than SMs, full-grid tile launches for the "
                                          "wider ones; plus one basis-state write per state"}
         del ust
 

@@ -230,12 +230,15 @@ sv_status sv_plan_fmas(sv_state *s, const sv_circuit *c, const double *params, c
                        double *fma_per_amp);
 
 /* Apply circs[b] (with parameters params[b], host FP64, either may repeat)
- * to states[b] for b < B, states of any widths, in ONE persistent launch:
- * every circuit is fused and planned into tile passes as by
- * sv_apply_circuit, and a cooperative kernel works through the queue of all
- * (state, pass, tile) items in pass order; a tile of pass p waits until pass
- * p-1 of its own state is complete (Sec. I motivates many independent
- * simulations: variational training evaluates many circuits).  Waits are
+ * to states[b] for b < B, states of any widths, in one call: every circuit
+ * is fused and planned into tile passes as by sv_apply_circuit.  The narrow
+ * states (passes with fewer tiles than the GPU has SMs) go through ONE
+ * persistent launch: a cooperative kernel works through the queue of all
+ * their (state, pass, tile) items in pass order, a tile of pass p waiting
+ * until pass p-1 of its own state is complete (Sec. I motivates many
+ * independent simulations: variational training evaluates many circuits).
+ * The wide states, and programs with tensor-core passes, follow as ordinary
+ * full-grid launches of their passes on the same stream.  Waits are
  * bounded by opt->timeout_cycles polls (~128 ns each; 0 = about 1 s); a wait
  * that runs out stops the launch and the next sv_synchronize on states[0]
  * returns SV_ETIMEOUT.  With opt->mode == SV_MODE_TILED_GRAPH the counter
