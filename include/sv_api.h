@@ -169,7 +169,12 @@ sv_status sv_set_basis(sv_state *s, uint64_t index);
 sv_status sv_mark_modified(sv_state *s);
 /* Copy 2^n amplitudes host -> device / device -> host (bytes must equal the
  * state size); synchronous w.r.t. the host.  Used for checkpoints and for
- * end-to-end runs that start from a host state. */
+ * end-to-end runs that start from a host state.  Page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister, e.g. a pinned torch tensor) aligned to
+ * 16 bytes is moved by a copy kernel whose SMs read or write it directly
+ * over the GPU's host link; other host memory goes through
+ * cudaMemcpyAsync.  Errors: SV_EINVAL (null pointer, size mismatch),
+ * SV_ECUDA. */
 sv_status sv_upload(sv_state *s, const void *host, size_t bytes);
 sv_status sv_download(sv_state *s, void *host, size_t bytes);
 /* Wait for all work enqueued on the state's stream; reports device-side

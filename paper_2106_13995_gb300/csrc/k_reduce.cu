@@ -72,6 +72,35 @@ __global__ void k_move_basis(typename Cx<R>::T *a, uint64_t from, uint64_t to, R
   a[to] = cmake(re, im);
 }
 
+// Bulk copy by the SMs, 16 bytes per thread and trip, four trips in flight:
+// used for host <-> device moves of page-locked host memory, which the GPU
+// reads and writes directly over its host link (the copy engines are not
+// involved, so their other traffic does not slow it).
+__global__ void __launch_bounds__(256) k_copy16(const int4 *__restrict__ src, int4 *__restrict__ dst, size_t n16) {
+  const size_t st = (size_t)gridDim.x * blockDim.x;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * st < n16; i += 4 * st) {
+    const int4 a = src[i], b = src[i + st], c = src[i + 2 * st], d = src[i + 3 * st];
+    dst[i] = a;
+    dst[i + st] = b;
+    dst[i + 2 * st] = c;
+    dst[i + 3 * st] = d;
+  }
+  for (; i < n16; i += st) dst[i] = src[i];
+}
+
+sv_status launch_copy16(sv_state *s, const void *src, void *dst, size_t bytes) {
+  if (bytes % 16 || ((uintptr_t)src | (uintptr_t)dst) % 16) return set_error(SV_EINVAL, "internal: unaligned copy");
+  if (bytes == 0) return SV_OK;
+  const size_t n16 = bytes / 16;
+  const size_t want = (n16 + 255) / 256;
+  const int grid = (int)std::max<size_t>(1, std::min<size_t>(want, (size_t)s->sm_count * 4));
+  k_copy16<<<grid, 256, 0, s->stream>>>(reinterpret_cast<const int4 *>(src), reinterpret_cast<int4 *>(dst), n16);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
 sv_status launch_move_basis(sv_state *s, uint64_t from, uint64_t to, cd amp) {
   if (s->dt == SV_C64)
     k_move_basis<float><<<1, 1, 0, s->stream>>>((float2 *)s->amps, from, to, (float)amp.real(), (float)amp.imag());

@@ -805,11 +805,26 @@ sv_status sv_mark_modified(sv_state *s) {
   return SV_OK;
 }
 
+// The device address of page-locked host memory (16-byte aligned), or null
+// for any other host pointer.
+static const void *mapped_host(const void *host) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, host) != cudaSuccess) {
+    cudaGetLastError();   // unregistered memory on older runtimes: not an error
+    return nullptr;
+  }
+  if (attr.type != cudaMemoryTypeHost || !attr.devicePointer || (uintptr_t)attr.devicePointer % 16) return nullptr;
+  return attr.devicePointer;
+}
+
 sv_status sv_upload(sv_state *s, const void *host, size_t bytes) {
   if (!s || !host) return set_error(SV_EINVAL, "null argument");
   if (bytes != ((size_t)1 << s->n) * amp_bytes(s->dt)) return set_error(SV_EINVAL, "size mismatch");
   s->basis_known = false;
-  SV_CUDA(cudaMemcpyAsync(s->amps, host, bytes, cudaMemcpyHostToDevice, s->stream));
+  if (const void *dev = mapped_host(host); dev && bytes % 16 == 0)
+    SV_TRY(launch_copy16(s, dev, s->amps, bytes));
+  else
+    SV_CUDA(cudaMemcpyAsync(s->amps, host, bytes, cudaMemcpyHostToDevice, s->stream));
   SV_CUDA(cudaStreamSynchronize(s->stream));
   return SV_OK;
 }
@@ -817,7 +832,10 @@ sv_status sv_upload(sv_state *s, const void *host, size_t bytes) {
 sv_status sv_download(sv_state *s, void *host, size_t bytes) {
   if (!s || !host) return set_error(SV_EINVAL, "null argument");
   if (bytes != ((size_t)1 << s->n) * amp_bytes(s->dt)) return set_error(SV_EINVAL, "size mismatch");
-  SV_CUDA(cudaMemcpyAsync(host, s->amps, bytes, cudaMemcpyDeviceToHost, s->stream));
+  if (const void *dev = mapped_host(host); dev && bytes % 16 == 0)
+    SV_TRY(launch_copy16(s, s->amps, const_cast<void *>(dev), bytes));
+  else
+    SV_CUDA(cudaMemcpyAsync(host, s->amps, bytes, cudaMemcpyDeviceToHost, s->stream));
   SV_CUDA(cudaStreamSynchronize(s->stream));
   return SV_OK;
 }

@@ -417,6 +417,10 @@ void drop_adjoint_programs(const sv_state *s);
 sv_status launch_set_basis(sv_state *s, uint64_t index);
 // psi[from] := 0, psi[to] := a (one thread; the state is a basis state)
 sv_status launch_move_basis(sv_state *s, uint64_t from, uint64_t to, cd a);
+// copy `bytes` (a multiple of 16, both pointers 16-byte aligned and
+// addressable by the device: device memory or mapped page-locked host
+// memory) by a grid-stride kernel on the state's stream
+sv_status launch_copy16(sv_state *s, const void *src, void *dst, size_t bytes);
 // Follow a basis state through gates that map it to a basis state times a
 // phase (permutations, diagonal and monomial gates, with controls); false,
 // leaving index and amp unspecified, as soon as one gate does not.
