@@ -782,6 +782,11 @@ sv_status sv_destroy(sv_state *s) {
   drop_adjoint_programs(s);
   drop_graphs(s);
   if (s->capture) cudaStreamDestroy(s->capture);
+  for (int k = 0; k < kFanStreams; k++) {
+    if (s->fan[k]) cudaStreamDestroy(s->fan[k]);
+    if (s->fan_join[k]) cudaEventDestroy(s->fan_join[k]);
+  }
+  if (s->fan_fork) cudaEventDestroy(s->fan_fork);
   if (s->staged) cudaEventDestroy(s->staged);
   if (s->pinned) cudaFreeHost(s->pinned);
   delete s;

@@ -3,6 +3,7 @@
 // autotuner that picks fusion width and tile size per circuit shape; and the
 // self-test of the bounded device wait.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -153,25 +154,69 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
       items += (nt + ch - 1) / ch;
     }
   const uint32_t nd = (uint32_t)desc.size();
-  // the wide states' passes, as ordinary launches on stream st
-  auto launch_wide = [&](cudaStream_t st) -> sv_status {
-    for (int b = 0; b < B; b++) {
-      if (!wide[b]) continue;
-      const CachedProgram &cp = *cps[b];
-      char *base = states[b]->ws + kWsProg;
-      for (size_t p = 0; p < cp.prog.passes.size(); p++) {
-        TilePass tp = cp.prog.passes[p];
-        tp.ops = reinterpret_cast<const TileOp *>(base + cp.lay.ops_off) + cp.op0s[p];
-        tp.mats = base + cp.lay.mats_off;
-        tp.coeffs = reinterpret_cast<const double *>(base + cp.lay.coeffs_off);
-        tp.v0 = states[b]->amps;
-        tp.nvec = 1;
-        tp.err = reinterpret_cast<uint32_t *>(states[b]->ws + kWsCtrl + kWsErrFlag);
-        const HostPass hp{cp.prog.ops.data() + cp.op0s[p], cp.prog.mats.data()};
-        SV_TRY(launch_any_pass(states[b], tp, 1, st, &hp));
-      }
+  // The wide states' passes, as ordinary launches.  The states are
+  // independent, so with two or more of them they are spread over the
+  // library's fan-out streams (longest first onto the least-loaded stream,
+  // load = tiles x passes), forked from st and joined back into it: one
+  // state's passes fill the waves another leaves partly empty, and a stream
+  // launches while another's kernel runs.  Recorded in a graph, the streams
+  // become parallel branches.
+  std::vector<int> wb;
+  std::vector<double> work(B, 0.0);
+  for (int b = 0; b < B; b++)
+    if (wide[b]) {
+      wb.push_back(b);
+      for (const TilePass &tp : cps[b]->prog.passes) work[b] += std::ldexp(1.0, tp.n - tp.m);
+    }
+  const int K = std::min<int>(kFanStreams, (int)wb.size());
+  std::vector<int> lane(B, 0);
+  if (K >= 2) {
+    for (int k = 0; k < K; k++)
+      if (!s0->fan[k]) SV_CUDA(cudaStreamCreateWithFlags(&s0->fan[k], cudaStreamNonBlocking));
+    if (!s0->fan_fork) SV_CUDA(cudaEventCreateWithFlags(&s0->fan_fork, cudaEventDisableTiming));
+    for (int k = 0; k < K; k++)
+      if (!s0->fan_join[k]) SV_CUDA(cudaEventCreateWithFlags(&s0->fan_join[k], cudaEventDisableTiming));
+    std::vector<int> order = wb;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    std::vector<double> load(K, 0.0);
+    for (int b : order) {
+      const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lane[b] = k;
+      load[k] += work[b];
+    }
+  }
+  auto launch_state = [&](int b, cudaStream_t st) -> sv_status {
+    const CachedProgram &cp = *cps[b];
+    char *base = states[b]->ws + kWsProg;
+    for (size_t p = 0; p < cp.prog.passes.size(); p++) {
+      TilePass tp = cp.prog.passes[p];
+      tp.ops = reinterpret_cast<const TileOp *>(base + cp.lay.ops_off) + cp.op0s[p];
+      tp.mats = base + cp.lay.mats_off;
+      tp.coeffs = reinterpret_cast<const double *>(base + cp.lay.coeffs_off);
+      tp.v0 = states[b]->amps;
+      tp.nvec = 1;
+      tp.err = reinterpret_cast<uint32_t *>(states[b]->ws + kWsCtrl + kWsErrFlag);
+      const HostPass hp{cp.prog.ops.data() + cp.op0s[p], cp.prog.mats.data()};
+      SV_TRY(launch_any_pass(states[b], tp, 1, st, &hp));
     }
     return SV_OK;
+  };
+  auto launch_wide = [&](cudaStream_t st) -> sv_status {
+    if (K < 2) {
+      for (int b : wb) SV_TRY(launch_state(b, st));
+      return SV_OK;
+    }
+    SV_CUDA(cudaEventRecord(s0->fan_fork, st));
+    for (int k = 0; k < K; k++) SV_CUDA(cudaStreamWaitEvent(s0->fan[k], s0->fan_fork, 0));
+    sv_status rc = SV_OK;
+    for (int b : wb)
+      if (rc == SV_OK) rc = launch_state(b, s0->fan[lane[b]]);
+    // join every stream back even after an error, so none is left forked
+    for (int k = 0; k < K; k++) {
+      SV_CUDA(cudaEventRecord(s0->fan_join[k], s0->fan[k]));
+      SV_CUDA(cudaStreamWaitEvent(st, s0->fan_join[k], 0));
+    }
+    return rc;
   };
   const bool use_graph = opt && opt->mode == SV_MODE_TILED_GRAPH;
   if (nd == 0) {

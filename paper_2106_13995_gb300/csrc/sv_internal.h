@@ -228,6 +228,9 @@ struct DeviceProgram {
 
 }  // namespace sv
 
+// streams over which a batched call spreads its wide states
+constexpr int kFanStreams = 4;
+
 struct sv_state {
   int n = 0;
   sv_dtype dt = SV_C64;
@@ -243,6 +246,11 @@ struct sv_state {
   size_t pinned_bytes = 0;
   cudaEvent_t staged = nullptr;     // last upload from `pinned` finished
   cudaStream_t capture = nullptr;   // library-owned stream used only to record CUDA graphs
+  // library-owned streams and fork/join events over which a batch spreads
+  // its independent wide states (sv_apply_circuit_batch), made on first use
+  cudaStream_t fan[kFanStreams] = {};
+  cudaEvent_t fan_fork = nullptr;
+  cudaEvent_t fan_join[kFanStreams] = {};
   uint64_t resident = 0;            // serial of the program in the workspace program area (0: none)
   // the state is known to be basis_amp |basis_index>: set by sv_set_basis,
   // kept by circuits of permutation and phase gates, cleared by every other
