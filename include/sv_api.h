@@ -243,7 +243,9 @@ sv_status sv_plan_fmas(sv_state *s, const sv_circuit *c, const double *params, c
  * until pass p-1 of its own state is complete (Sec. I motivates many
  * independent simulations: variational training evaluates many circuits).
  * The wide states, and programs with tensor-core passes, follow as ordinary
- * full-grid launches of their passes on the same stream.  Waits are
+ * full-grid launches of their passes, spread over up to four library-owned
+ * streams forked from the states' stream after that launch and joined back
+ * into it (the call stays stream-ordered).  Waits are
  * bounded by opt->timeout_cycles polls (~128 ns each; 0 = about 1 s); a wait
  * that runs out stops the launch and the next sv_synchronize on states[0]
  * returns SV_ETIMEOUT.  With opt->mode == SV_MODE_TILED_GRAPH the counter
