@@ -15,15 +15,19 @@
 //     while it waits for its loads or its MMAs the other three groups
 //     gather, split and scatter (16 warps per SM: the register file allows
 //     no more, and shared memory no more tile buffers next to the B
-//     operands);
+//     operands); when a group starts a tile it asks L2 for its next one, so
+//     that load waits on L2 rather than HBM;
 //   - the B operands of all blocks of the pass are copied into shared memory
 //     once per CTA and stay there for all its tiles.
 // The tile's shared-memory layout keeps each even/odd amplitude pair
 // together (16-byte units) and XORs slot bits 1..3 with tile bits 4..6 and
-// 8..10, so unit loads and stores are conflict-free and a warp's gathers of
-// one member from 32 groups spread over the banks (the host picks which tile
-// bits the lane bits address, TileOp.tbpos).  When tile bit 0 is a target it
-// is the block's first target, and members are gathered in 16-byte pairs.
+// 8..10, so unit loads and stores are conflict-free.  Each block after the
+// first sees the tile through its own layout, tile bit 0 swapped with its
+// first target, so the members of a row move as 16-byte pairs; a block
+// scatters into the next block's layout (in pairs when the two share that
+// first target; the last one into the store's layout), and the host picks
+// the first targets and which tile bits the lane bits address
+// (TileOp.tbpos) so that gathers and scatters spread over the banks.
 //
 // Every wait is bounded: a wait that runs out raises the error flag, the
 // group stops, and before the CTA exits it waits (bounded) for its MMAs and
@@ -64,7 +68,8 @@ __host__ __device__ constexpr uint32_t tcp_swz(uint32_t l) {
 
 // Per-block set-up, computed on the host and passed in the launch's
 // parameter block (warp-uniform reads): each block's member offsets
-// tcp_swz(target bits of y) and the offset contributed by each row bit.
+// tcp_swz(layout(target bits of y)) and the offset contributed by each row
+// bit, under the block's own layout (gather) and the next one's (scatter).
 struct TcpTable {
   uint32_t soff[kTcpMaxBlocks][32];   // gather: the block's own layout
   uint32_t rbit[kTcpMaxBlocks][8];
