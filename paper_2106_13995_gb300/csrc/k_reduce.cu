@@ -346,15 +346,24 @@ __global__ void __launch_bounds__(kDiagThreads) k_expect_diag(const int4 *__rest
 #pragma unroll
     for (int i = 0; i < NPAT; i++) sq[wi][i][lane] = q[i];
     __syncwarp();
-    R part = 0;
+    // two accumulators each, so the sums are not one serial chain
+    R part0 = 0, part1 = 0;
     for (uint32_t g = 0; g < A.ng; g++) {
-      R ck = 0;
-      for (uint32_t t = A.tstart[g]; t < A.tstart[g + 1]; t++)
-        ck += (__popcll(x0 & A.zm[t]) & 1) ? -A.c[t] : A.c[t];
+      R ck0 = 0, ck1 = 0;
+      uint32_t t = A.tstart[g];
+      const uint32_t te = A.tstart[g + 1];
+      for (; t + 1 < te; t += 2) {
+        ck0 += (__popcll(x0 & A.zm[t]) & 1) ? -A.c[t] : A.c[t];
+        ck1 += (__popcll(x0 & A.zm[t + 1]) & 1) ? -A.c[t + 1] : A.c[t + 1];
+      }
+      if (t < te) ck0 += (__popcll(x0 & A.zm[t]) & 1) ? -A.c[t] : A.c[t];
+      const R ck = ck0 + ck1;
       const R qv = sq[wi][A.gpat[g]][lane];
-      part += (__popc((uint32_t)lane & A.lm[g]) & 1) ? -ck * qv : ck * qv;
+      const R term = (__popc((uint32_t)lane & A.lm[g]) & 1) ? -ck * qv : ck * qv;
+      if (g & 1) part1 += term;
+      else part0 += term;
     }
-    acc += (double)part;
+    acc += (double)part0 + (double)part1;
   }
   block_sum_to(acc, partial + blockIdx.x);
 }
