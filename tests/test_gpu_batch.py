@@ -164,6 +164,40 @@ def test_uneven_circuits_tensor_core_modes(svlib, oracle, prec):
         assert inf <= 1e-5, (c.name, prec, inf)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_with_wide_states_on_forked_streams(svlib, oracle, prec):
+    """One graph-recorded batched call over narrow states (the persistent
+    queue) and several wide ones (full-grid passes spread over the library's
+    forked streams; with split-BF16 the pipelined tensor-core passes), played
+    twice: the narrow states match the FP64 oracle, and every state matches
+    its own single-circuit run bit for bit (the kernels are deterministic,
+    whatever stream runs them)."""
+    from paper_2106_13995_gb300 import _native as N
+    narrow = small_uneven(6, 10, 15, 12, seed=21)
+    wide = small_uneven(5, 21, 22, 8, seed=22)
+    circs = narrow + wide
+    opts = svlib.options(prec=prec, mode=N.SV_MODE_TILED_GRAPH)
+    single = svlib.options(prec=prec)
+    want = []
+    for c in circs:
+        s = svlib.StateVector(c.n_qubits, "c64").set_basis(0).apply_circuit(c, opts=single)
+        want.append(s.numpy())
+        s.close()
+    states = [svlib.StateVector(c.n_qubits, "c64") for c in circs]
+    for rep in range(2):
+        for st in states:
+            st.set_basis(0)
+        batch_apply(svlib, states, circs, opts)
+        for i, (c, st) in enumerate(zip(circs, states)):
+            got = st.numpy()
+            assert np.array_equal(got, want[i]), (rep, c.name)
+            if c.n_qubits <= 15:
+                inf, _ = fidelity_metrics(oracle.run(c), got)
+                assert inf <= (1e-5 if prec else 1e-9), (c.name, inf)
+    for st in states:
+        st.close()
+
+
 @pytest.mark.parametrize("graph", [False, True])
 def test_batch_beyond_program_cache_bound(svlib, graph):
     """A batch of more distinct circuits than the program cache holds: the
