@@ -78,7 +78,8 @@ def test_pipelined_layout_chains(svlib, oracle):
     pair gathers and scatters), checked amplitude by amplitude against the
     FP64 oracle from a random state; the error budget grows with the
     number of blocks."""
-    for seed, (n, count, span) in enumerate([(13, 12, 7), (14, 16, 8), (16, 24, 9), (18, 20, 12)]):
+    # 12 qubits: a single tile, so three of the CTA's four groups get none
+    for seed, (n, count, span) in enumerate([(12, 10, 12), (13, 12, 7), (14, 16, 8), (16, 24, 9), (18, 20, 12)]):
         rng = np.random.default_rng(seed)
         c = W.block_chain(n, count, seed + 40, span)
         psi0 = W.random_state(n, rng)
