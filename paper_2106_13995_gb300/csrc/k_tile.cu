@@ -383,8 +383,93 @@ sv_status launch_tile_pass(sv_state *s, const TilePass &p, int batch) {
   return launch_tile_pass_on(s, p, batch, s->stream);
 }
 
+// K11: a permutation pass (kPassTable; paper Sec. III's reversible
+// multipliers).  One CTA per tile (and per state of a batch): the tile is
+// loaded into shared memory, then every output amplitude is read from the
+// slot the pass's gather table names and stored -- one move per amplitude
+// for all the pass's blocks, no arithmetic.  The table is the one for the
+// values the pass's global control qubits take in this tile.
+template <typename R>
+__global__ void __launch_bounds__(kTilePassThreads) k_tile_tperm(const __grid_constant__ TilePass P) {
+  using C = typename Cx<R>::T;
+  using UN = Unit<R>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *v = reinterpret_cast<C *>(smem_raw);
+  const uint32_t TS = 1u << P.m;
+  const uint64_t base = tile_base(P, blockIdx.x);
+  C *g0 = reinterpret_cast<C *>(P.tbl0 ? P.tbl0[blockIdx.y] : P.v0);
+  const unsigned char *blk = static_cast<const unsigned char *>(P.mats) + 16 * (size_t)P.mat0;
+  const uint32_t g = *reinterpret_cast<const uint32_t *>(blk);
+  uint32_t var = 0;
+  for (uint32_t i = 0; i < g; i++) var |= (uint32_t)((base >> blk[4 + i]) & 1ull) << i;
+  const uint16_t *tab = reinterpret_cast<const uint16_t *>(blk + 16) + (size_t)var * TS;
+  const uint32_t nunits = TS / UN::APU;
+  const uint32_t segmask = (1u << P.L) - 1;
+  const uint32_t lthr = threadIdx.x * UN::APU;
+  const uint64_t gthr = base | (lthr & segmask) | spread_hi(P, lthr & ~segmask);
+  const uint32_t tstep = blockDim.x * UN::APU;
+  auto goff = [&](uint32_t i) -> uint64_t {
+    const uint32_t lt = i * tstep;
+    return gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
+  };
+  // eight units per thread and batch, so eight loads (and eight table
+  // reads) are in flight at a time
+  constexpr uint32_t kBatch = 8;
+  for (uint32_t i0 = 0; i0 * blockDim.x + threadIdx.x < nunits; i0 += kBatch) {
+    int4 r[kBatch];
+#pragma unroll
+    for (uint32_t j = 0; j < kBatch; j++)
+      if ((i0 + j) * blockDim.x + threadIdx.x < nunits) r[j] = __ldcs(reinterpret_cast<const int4 *>(&g0[goff(i0 + j)]));
+#pragma unroll
+    for (uint32_t j = 0; j < kBatch; j++) {
+      const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
+      if (u < nunits) UN::put(v, u * UN::APU, r[j]);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i0 = 0; i0 * blockDim.x + threadIdx.x < nunits; i0 += kBatch) {
+    uint16_t src[kBatch][UN::APU];
+#pragma unroll
+    for (uint32_t j = 0; j < kBatch; j++) {
+      const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
+      if (u < nunits) {
+#pragma unroll
+        for (uint32_t a = 0; a < UN::APU; a++) src[j][a] = __ldg(tab + u * UN::APU + a);
+      }
+    }
+#pragma unroll
+    for (uint32_t j = 0; j < kBatch; j++) {
+      const uint32_t u = (i0 + j) * blockDim.x + threadIdx.x;
+      if (u < nunits) {
+        C out[UN::APU];
+#pragma unroll
+        for (uint32_t a = 0; a < UN::APU; a++) out[a] = v[sw<R>(src[j][a])];
+        __stcs(reinterpret_cast<int4 *>(&g0[goff(i0 + j)]), *reinterpret_cast<const int4 *>(out));
+      }
+    }
+  }
+}
+
+static sv_status launch_tile_tperm(sv_state *s, const TilePass &p, int batch, cudaStream_t stream) {
+  if (p.nvec != 1 || p.m > 16) return set_error(SV_EINVAL, "internal: permutation pass needs one vector and m <= 16");
+  const size_t smem = tile_smem(s->dt, p.m, 1);
+  if (smem > (200u << 10)) return set_error(SV_EINVAL, "tile too large for shared memory");
+  const void *fn = s->dt == SV_C64 ? (const void *)k_tile_tperm<float> : (const void *)k_tile_tperm<double>;
+  SV_TRY(func_attr_once(fn, s->device, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 << 10));
+  dim3 grid((unsigned)(1ull << (p.n - p.m)), (unsigned)batch);
+  const int threads = tile_threads(p.m, s->dt);
+  if (s->dt == SV_C64)
+    k_tile_tperm<float><<<grid, threads, smem, stream>>>(p);
+  else
+    k_tile_tperm<double><<<grid, threads, smem, stream>>>(p);
+  g_launches++;
+  SV_CUDA(cudaGetLastError());
+  return SV_OK;
+}
+
 sv_status launch_tile_pass_on(sv_state *s, const TilePass &p, int batch, cudaStream_t stream,
                               const HostPass *host) {
+  if (p.flags & kPassTable) return launch_tile_tperm(s, p, batch, stream);
   if (p.flags & kPassHasTC) {
     if (s->dt != SV_C64 || p.m != kTcTileM || batch != 1 || p.nvec != 1)
       return set_error(SV_EINVAL, "internal: tensor-core tile pass needs one complex64 vector and 12-qubit tiles");

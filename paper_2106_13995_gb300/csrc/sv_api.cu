@@ -174,7 +174,8 @@ static void set_thread_positions(TileOp &op, uint32_t fixed, int m, sv_dtype dt)
 // permutation matrix with exact 0/1 entries
 bool permutation_of(const std::vector<cd> &U, int k, int *perm) {
   const int d = 1 << k;
-  uint32_t rows = 0;
+  if (k > 6) return false;
+  uint64_t rows = 0;
   for (int c = 0; c < d; c++) {
     int r1 = -1;
     for (int r = 0; r < d; r++) {
@@ -183,8 +184,8 @@ bool permutation_of(const std::vector<cd> &U, int k, int *perm) {
       if (u != cd(1.0) || r1 >= 0) return false;
       r1 = r;
     }
-    if (r1 < 0 || ((rows >> r1) & 1u)) return false;
-    rows |= 1u << r1;
+    if (r1 < 0 || ((rows >> r1) & 1ull)) return false;
+    rows |= 1ull << r1;
     perm[c] = r1;
   }
   return true;
@@ -202,6 +203,95 @@ void put_pairs_c64(std::vector<uint8_t> &pool, const cd *U, int k) {
 }
 
 // Convert one planned pass into TilePass + TileOps (+ matrices).
+// A pass whose every block only moves amplitudes (0/1 permutation blocks:
+// X, CNOT, Toffoli, multi-controlled X and their products, paper Sec. III's
+// multipliers) is composed on the host into one gather table per setting of
+// the pass's global control qubits: the tile kernel then reads each
+// amplitude from its source slot (out[y] = in[table[y]]), one move per
+// amplitude for the whole pass instead of a complex matrix product per
+// block.  Table block in the matrix pool (16-byte aligned): uint32 g, int8
+// global qubit positions[8], 4 bytes padding, then 2^g tables of 2^m uint16
+// (table v serves the tiles whose global control qubits read v's bits).
+// Returns false (nothing appended) if the pass does not qualify.
+static bool table_pass(const PassPlan &P, const BuildCtx &b, const int *loc, int m, std::vector<uint8_t> &pool,
+                       uint32_t &mat0) {
+  if (b.nvec != 1 || m > 16 || P.ops.empty()) return false;
+  struct PB {
+    uint32_t lc = 0, tmask = 0;
+    uint64_t gc = 0;
+    int k = 0;
+    int t[6];
+    int perm[64];
+  };
+  std::vector<PB> pbs;
+  uint64_t gall = 0;
+  for (const Block &blk : P.ops) {
+    if ((blk.kind != TOP_DENSE && blk.kind != TOP_TC) || blk.inst >= 0 || blk.param >= 0 || blk.vmask != 1 ||
+        blk.xmask || blk.qubits.size() > 6)
+      return false;
+    PB pb;
+    pb.k = (int)blk.qubits.size();
+    if (!permutation_of(blk.U, pb.k, pb.perm)) return false;
+    for (int j = 0; j < pb.k; j++) {
+      if (loc[blk.qubits[j]] < 0) return false;
+      pb.t[j] = loc[blk.qubits[j]];
+      pb.tmask |= 1u << pb.t[j];
+    }
+    for (int q : blk.controls) {
+      if (loc[q] >= 0) pb.lc |= 1u << loc[q];
+      else pb.gc |= 1ull << q;
+    }
+    gall |= pb.gc;
+    pbs.push_back(pb);
+  }
+  const int g = __builtin_popcountll(gall);
+  const uint32_t N = 1u << m;
+  const size_t bytes = 16 + ((size_t)N << g) * sizeof(uint16_t);
+  // at most 5 global control qubits, and tables take at most half the
+  // workspace's program area
+  if (g > 5 || pool.size() + bytes > kWsProgBytes / 2) return false;
+  int gq[8] = {0};
+  {
+    int i = 0;
+    for (uint64_t x = gall; x; x &= x - 1) gq[i++] = __builtin_ctzll(x);
+  }
+  std::vector<uint32_t> x(N);
+  std::vector<uint16_t> tab((size_t)N << g);
+  for (uint32_t v = 0; v < (1u << g); v++) {
+    uint64_t gset = 0;
+    for (int i = 0; i < g; i++)
+      if ((v >> i) & 1u) gset |= 1ull << gq[i];
+    for (uint32_t l = 0; l < N; l++) x[l] = l;
+    for (const PB &pb : pbs) {
+      if (pb.gc & ~gset) continue;   // a global control reads 0 in these tiles
+      for (uint32_t l = 0; l < N; l++) {
+        const uint32_t xv = x[l];
+        if ((xv & pb.lc) != pb.lc) continue;
+        int c = 0;
+        for (int j = 0; j < pb.k; j++) c |= (int)((xv >> pb.t[j]) & 1u) << j;
+        const int r = pb.perm[c];
+        if (r == c) continue;
+        uint32_t nv = xv & ~pb.tmask;
+        for (int j = 0; j < pb.k; j++) nv |= (uint32_t)((r >> j) & 1) << pb.t[j];
+        x[l] = nv;
+      }
+    }
+    // the amplitude at tile slot l ends at x[l]: gather out[x[l]] = in[l]
+    uint16_t *t = tab.data() + (size_t)v * N;
+    for (uint32_t l = 0; l < N; l++) t[x[l]] = (uint16_t)l;
+  }
+  while (pool.size() % 16) pool.push_back(0);
+  mat0 = (uint32_t)(pool.size() / 16);
+  uint8_t hdr[16] = {0};
+  const uint32_t g32 = (uint32_t)g;
+  std::memcpy(hdr, &g32, 4);
+  for (int i = 0; i < g; i++) hdr[4 + i] = (uint8_t)gq[i];
+  pool.insert(pool.end(), hdr, hdr + 16);
+  const uint8_t *tb = reinterpret_cast<const uint8_t *>(tab.data());
+  pool.insert(pool.end(), tb, tb + tab.size() * sizeof(uint16_t));
+  return true;
+}
+
 // First targets (tile positions) of the blocks of a pass the pipelined
 // tensor-core kernel runs.  Block j > 0 is gathered under a layout whose
 // pair bit is its first target c_j; it scatters in 16-byte pairs when
@@ -257,6 +347,12 @@ sv_status emit_pass(DeviceProgram &prog, const PassPlan &P, const BuildCtx &b,
     if (loc[q] < 0) tp.out_pos[no++] = (int8_t)q;
   op0s.push_back((uint32_t)prog.ops.size());
   const size_t ab = amp_bytes(b.dt);
+  if (batch_mat_off.empty() && table_pass(P, b, loc, tp.m, prog.mats, tp.mat0)) {
+    tp.nops = 0;
+    tp.flags |= kPassTable;
+    prog.passes.push_back(tp);
+    return SV_OK;
+  }
   // a pass for the pipelined tensor-core kernel: its blocks' first targets
   std::vector<int> tc_first;
   {

@@ -121,7 +121,9 @@ static sv_status run_batch(sv_state *const *states, int B, const sv_circuit *con
     uint64_t min_tiles = ~0ull;
     for (const TilePass &tp : cps[b]->prog.passes) min_tiles = std::min<uint64_t>(min_tiles, (uint64_t)1 << (tp.n - tp.m));
     bool has_tc = false;
-    for (const TilePass &tp : cps[b]->prog.passes) has_tc |= (tp.flags & (kPassTC | kPassHasTC)) != 0;
+    // (tensor-core and permutation passes have kernels of their own, which
+    // the persistent queue does not run)
+    for (const TilePass &tp : cps[b]->prog.passes) has_tc |= (tp.flags & (kPassTC | kPassHasTC | kPassTable)) != 0;
     wide[b] = !cps[b]->prog.passes.empty() && (has_tc || min_tiles >= (uint64_t)s0->sm_count);
   }
   // descriptors in wave order: pass 0 of every state, then pass 1, ...

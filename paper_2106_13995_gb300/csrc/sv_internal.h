@@ -110,6 +110,10 @@ struct TileInline {
 constexpr uint32_t kPassTC = 0x100;
 // TilePass.flags: the pass contains TOP_TC ops (allocate TMEM); mode in bits 9..10
 constexpr uint32_t kPassHasTC = 0x8;
+// TilePass.flags: a permutation pass with no ops: every amplitude of a tile
+// moves by a gather table (16-byte index mat0 of its block in the matrix
+// pool; k_tile_tperm)
+constexpr uint32_t kPassTable = 0x800;
 constexpr int kTcTileM = 12;          // tile size that gives M = 128 groups for a 5-qubit block
 size_t tc_tile_smem(sv_prec mode);    // shared memory of a 12-qubit tile pass with TOP_TC ops
 struct TilePass {

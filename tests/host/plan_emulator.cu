@@ -30,6 +30,31 @@ static uint32_t ins0_mask_h(uint32_t x, uint32_t f) {
   return x;
 }
 
+// permutation passes met by plan_emulate so far (read and reset by
+// table_pass_count)
+static int g_table_passes = 0;
+extern "C" int table_pass_count() {
+  const int n = g_table_passes;
+  g_table_passes = 0;
+  return n;
+}
+
+// A permutation pass (kPassTable): the tile's amplitudes moved through the
+// gather table for the tile's global control values, out[y] = in[table[y]].
+template <typename V>
+static void apply_table_pass(const DeviceProgram &prog, const TilePass &tp, uint64_t base, V &v) {
+  const uint8_t *blk = prog.mats.data() + 16 * (size_t)tp.mat0;
+  uint32_t g;
+  std::memcpy(&g, blk, 4);
+  uint32_t var = 0;
+  for (uint32_t i = 0; i < g; i++) var |= (uint32_t)((base >> blk[4 + i]) & 1ull) << i;
+  const uint32_t TS = 1u << tp.m;
+  const uint16_t *tab = reinterpret_cast<const uint16_t *>(blk + 16) + (size_t)var * TS;
+  V w(v.size());
+  for (uint32_t y = 0; y < TS; y++) w[y] = v[tab[y]];
+  v.swap(w);
+}
+
 // returns the number of passes, or -1 (message printed)
 extern "C" int plan_emulate(const sv_circuit *c, double *psi_, int fusion_k, int m, int L, int *n_blocks,
                             int merge) {
@@ -74,6 +99,7 @@ extern "C" int plan_emulate(const sv_circuit *c, double *psi_, int fusion_k, int
   for (size_t pi = 0; pi < prog.passes.size(); pi++) {
     const TilePass &tp = prog.passes[pi];
     const uint32_t TS = 1u << tp.m;
+    g_table_passes += (tp.flags & kPassTable) ? 1 : 0;
     for (uint64_t t = 0; t < (1ull << (n - tp.m)); t++) {
       uint64_t base = 0;
       for (int j = 0; j < n - tp.m; j++) base |= ((t >> j) & 1ull) << tp.out_pos[j];
@@ -85,6 +111,7 @@ extern "C" int plan_emulate(const sv_circuit *c, double *psi_, int fusion_k, int
       }
       std::vector<cx> v(TS);
       for (uint32_t l = 0; l < TS; l++) v[l] = psi[gi[l]];
+      if (tp.flags & kPassTable) apply_table_pass(prog, tp, base, v);
       for (int oi = 0; oi < tp.nops; oi++) {
         const TileOp &op = prog.ops[op0s[pi] + oi];
         const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);
@@ -479,6 +506,7 @@ extern "C" int tc_program_emulate(const sv_circuit *c, double *psi_, int *npure,
       }
       std::vector<cx> v(TS);
       for (uint32_t l = 0; l < TS; l++) v[l] = psi[gi[l]];
+      if (tp.flags & kPassTable) apply_table_pass(prog, tp, gbase, v);
       for (int oi = 0; oi < tp.nops; oi++) {
         const TileOp &op = prog.ops[cp->op0s[pi] + oi];
         const uint64_t gcm = (uint64_t)op.gcmask_lo | ((uint64_t)op.gcmask_hi << 32);

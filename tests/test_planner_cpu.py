@@ -102,6 +102,29 @@ def test_merge_in_passes_matches_oracle(emu, oracle, fk):
     assert oracle.infidelity(want, got) <= 1e-12
 
 
+def test_permutation_passes_as_tables(emu, oracle):
+    """Passes whose blocks are all 0/1 permutations (the multiplier's X,
+    CNOT, Toffoli and C^3X) become gather tables composed on the host, one
+    per setting of the pass's global control qubits; small tiles leave many
+    controls global.  Run on the CPU the programs match the oracle exactly,
+    with Hadamard inputs too (the first pass then keeps its dense ops)."""
+    emu.table_pass_count.restype = C.c_int
+    emu.table_pass_count()
+    total_h_tables = [0]
+    for c in (W.multiplier(2), W.multiplier(2, hadamard_inputs=True), W.multiplier(3)):
+        want = oracle.run(c)
+        for fk, m in ((3, 9), (2, 6), (3, 5), (1, 4)):
+            got, npass, nb = run(emu, c, fk, min(m, c.n_qubits), 2)
+            tables = emu.table_pass_count()
+            if not c.name.endswith("_h"):
+                assert tables == npass, (c.name, fk, m, tables, npass)
+            else:
+                total_h_tables[0] += tables
+            assert oracle.infidelity(want, got) <= 1e-12, (c.name, fk, m)
+            assert np.max(np.abs(got - want)) <= 1e-12, (c.name, fk, m)
+    assert total_h_tables[0] > 0   # smaller tiles split H from the permutations
+
+
 def test_thread_positions_cover_every_group(emu):
     """The plan-time thread-bit positions of complex64 tile ops: with the
     trip map of the launch's thread count (and of the 512-thread persistent
@@ -109,7 +132,10 @@ def test_thread_positions_cover_every_group(emu):
     16 lanes of a wavefront reach 16 bank rows."""
     from paper_2106_13995_gb300 import sim
     for c, fk, m in ((W.grid_random(4, 5, 10, 1), 3, 13), (W.grid_random(4, 4, 10, 2), 2, 12),
-                     (W.random_gate_circuit(14, 120, seed=5), 3, 12), (W.multiplier(3), 3, 10),
+                     (W.random_gate_circuit(14, 120, seed=5), 3, 12),
+                     # (Hadamard inputs: the multiplier's own passes are
+                     # permutation tables and carry no tile ops)
+                     (W.multiplier(3, hadamard_inputs=True), 3, 10),
                      (W.random_gate_circuit(12, 80, seed=9), 1, 9)):
         mm = sim.marshal(c)
         spread = C.c_int()
@@ -125,7 +151,7 @@ def test_op_setup_records_match_direct_slots(emu):
     touches in those trips."""
     from paper_2106_13995_gb300 import sim
     for c, m in ((W.grid_random(4, 5, 10, 1), 13), (W.random_gate_circuit(14, 120, seed=5), 12),
-                 (W.random_gate_circuit(11, 60, seed=2), 9), (W.multiplier(3), 10)):
+                 (W.random_gate_circuit(11, 60, seed=2), 9), (W.multiplier(3, hadamard_inputs=True), 10)):
         mm = sim.marshal(c)
         assert emu.check_op_pre(C.addressof(mm.c), min(m, c.n_qubits), 3) > 0, c.name
 
