@@ -412,9 +412,9 @@ __global__ void __launch_bounds__(kTilePassThreads) k_tile_tperm(const __grid_co
     const uint32_t lt = i * tstep;
     return gthr | (lt & segmask) | spread_hi(P, lt & ~segmask);
   };
-  // eight units per thread and batch, so eight loads (and eight table
-  // reads) are in flight at a time
-  constexpr uint32_t kBatch = 8;
+  // sixteen units per thread and batch, so sixteen loads (and table reads)
+  // are in flight at a time
+  constexpr uint32_t kBatch = 16;
   for (uint32_t i0 = 0; i0 * blockDim.x + threadIdx.x < nunits; i0 += kBatch) {
     int4 r[kBatch];
 #pragma unroll
