@@ -206,7 +206,10 @@ sv_status sv_apply_gate(sv_state *s, const int32_t *targets, int k, const int32_
  *   params: host FP64 vector of c->n_params (may be NULL if none is used).
  *   opt:    may be NULL (defaults).
  * Fused blocks whose matrix is a 0/1 permutation (CNOT, Toffoli, C^3X and
- * their products) only move amplitudes inside the tile; a state known to be
+ * their products) only move amplitudes inside the tile: a pass made only of
+ * such blocks is composed on the host into one gather table per setting of
+ * its global control qubits (at most 5 of them, tables within half the
+ * program area) and moves each amplitude once, exactly; a state known to be
  * a basis state (see sv_set_basis) takes no pass at all when every gate
  * maps basis states to basis states.
  * Errors: SV_EINVAL (malformed op, width mismatch), SV_ENOMEM (program does
