@@ -558,7 +558,7 @@ def main():
         th_ = timed(lambda: (ms_.set_basis(0), ms_.apply_circuit(mmh)), 2) / 2
         out["multiplier"] = {"n_qubits": 29, "native_ops": len(mc.ops), "basis_runs": 64,
                              "runs_per_s": 64 / tm_, "gates_per_s": 64 * len(mc.ops) / tm_,
-                             "path": "tile passes whose blocks are permutation ops (no arithmetic)",
+                             "path": "tile passes composed into permutation tables (one move per amplitude, no arithmetic)",
                              "basis_fast_path": {"runs_per_s": 64 / tf_, "gates_per_s": 64 * len(mc.ops) / tf_,
                                                  "path": "basis state followed on the host, two amplitudes "
                                                          "rewritten; each run includes the 4 GiB basis-state "
