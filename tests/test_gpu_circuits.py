@@ -291,3 +291,26 @@ def test_program_cache_reuse_and_params(svlib, oracle):
         s.set_basis(0).apply_circuit(m, params=p)
         inf, _ = fidelity_metrics(oracle.run(c, params=p), s.numpy())
         assert inf <= 1e-12
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_permutation_table_passes_move_random_states_exactly(svlib, oracle, dt):
+    """Multipliers on a random dense state: every pass is made of 0/1
+    permutation blocks, so the library runs them as gather-table passes.
+    Moving amplitudes is exact, so the result equals the FP64 oracle applied
+    to the same (rounded) input bit for bit -- with the default tiles and
+    with small tiles that leave several controls outside the tile (one
+    table per setting of them)."""
+    rng = np.random.default_rng(77)
+    for nbits in (2, 3):
+        c = W.multiplier(nbits)
+        n = c.n_qubits
+        psi0 = W.random_state(n, rng)
+        cast = psi0.astype(np.complex64 if dt == "c64" else np.complex128)
+        want = oracle.run(c, cast.astype(np.complex128))
+        for tile_m in (0, 6):
+            s = svlib.StateVector(n, dt).load(psi0)
+            s.apply_circuit(c, opts=svlib.options(tile_m=tile_m))
+            got = s.numpy().astype(np.complex128)
+            assert np.array_equal(got, want), (nbits, dt, tile_m, float(np.max(np.abs(got - want))))
+            s.close()
